@@ -1,0 +1,87 @@
+"""Model-level pins for the oracle (slower: tens of seconds in total).
+
+* Eq. 16/17 source: a flat interface keeps exactly the same coexistence
+  densities for any kappa (the source changes the tangential pressure only),
+  while droplets obey the Laplace law with sigma proportional to 1 - kappa
+  (Sec. 2, after Eq. 17).  A wrong trace or pxx coefficient in Eq. 16, or the
+  wrong sign of the Eq. 17 prefactor, breaks one of the two.
+* Geometric wetting (Sec. 4): a droplet settles at the prescribed angle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+CS = O.carnahan_starling()
+TC, _ = O.cs_critical(CS)
+T = 0.8 * TC
+RV, RL = O.coexistence(CS, T)
+
+
+def _slab(nx, ny, half):
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    return 0.5 * (RL + RV) - 0.5 * (RL - RV) * np.tanh(2 * (np.abs(y - ny / 2 + 0.5) - half) / 3.0)
+
+
+def test_kappa_leaves_flat_interface_densities_unchanged():
+    out = []
+    for kappa in (0.0, 0.5, 0.9):
+        s = O.Sim(4, 64, CS, T, tau=1.0, walls=False, kappa=kappa)
+        s.set_rho(_slab(4, 64, 16))
+        assert s.step(4000) == 0
+        r = s.rho()
+        out.append((r[32, 0], r[0, 0]))
+    for rl, rv in out[1:]:
+        assert rl == pytest.approx(out[0][0], rel=1e-10)
+        assert rv == pytest.approx(out[0][1], rel=1e-10)
+    # the flat-interface densities are those of the method, close to Maxwell's
+    assert out[0][0] == pytest.approx(RL, rel=0.02)
+    assert out[0][1] == pytest.approx(RV, rel=0.2)
+
+
+def _laplace(kappa, radii=(10, 13, 16, 20), n=64, steps=2500):
+    inv, dps = [], []
+    for R in radii:
+        s = O.Sim(n, n, CS, T, tau=1.0, walls=False, kappa=kappa)
+        y, x = np.mgrid[0:n, 0:n].astype(float)
+        r = np.hypot(x - n / 2 + 0.5, y - n / 2 + 0.5)
+        s.set_rho(0.5 * (RL + RV) - 0.5 * (RL - RV) * np.tanh(2 * (r - R) / 3.0))
+        assert s.step(steps) == 0
+        rho = s.rho()
+        rin, rout = rho[n // 2, n // 2], rho[0, 0]
+        Re = math.sqrt(((rho - rout) / (rin - rout)).sum() / math.pi)  # equimolar radius
+        inv.append(1.0 / Re)
+        dps.append(O.pressure(CS, T, rin) - O.pressure(CS, T, rout))
+    A = np.vstack([inv, np.ones(len(inv))]).T
+    (sigma, b), *_ = np.linalg.lstsq(A, np.array(dps), rcond=None)
+    pred = A @ [sigma, b]
+    r2 = 1 - ((dps - pred) ** 2).sum() / ((dps - np.mean(dps)) ** 2).sum()
+    return sigma, b, r2, np.array(dps)
+
+
+@pytest.mark.slow
+def test_laplace_law_and_sigma_scales_with_one_minus_kappa():
+    s0, b0, r20, dp0 = _laplace(0.0)
+    s5, b5, r25, dp5 = _laplace(0.5)
+    for sig, b, r2, dp in ((s0, b0, r20, dp0), (s5, b5, r25, dp5)):
+        assert sig > 0 and r2 > 0.99
+        assert abs(b) < 0.1 * dp.min()
+    assert s5 / s0 == pytest.approx(0.5, rel=0.1)
+
+
+def _settle(theta_deg, steps, nx=100, ny=60, R0=20):
+    rm = O.rho_max(CS, T, RL)
+    s = O.Sim(nx, ny, CS, T, tau=1.0, theta=math.radians(theta_deg), rho_max_=rm)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    r = np.hypot(x - nx / 2, y - 1.0)
+    s.set_rho(0.5 * (RL + RV) - 0.5 * (RL - RV) * np.tanh(2 * (r - R0) / 3.0))
+    assert s.step(steps) == 0
+    return math.degrees(s.contact_angle(0, 0, nx, 0.5 * (RL + RV))[0])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("theta_deg,steps,tol", [(90.0, 2000, 1.0), (60.0, 4000, 3.0), (120.0, 4000, 3.0)])
+def test_geometric_static_angle(theta_deg, steps, tol):
+    assert abs(_settle(theta_deg, steps) - theta_deg) < tol
