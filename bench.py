@@ -1,0 +1,345 @@
+"""Throughput benchmark of the pseudo-potential D2Q9 step (one JSON line).
+
+Default workload: the 4096 x 2048 large-density-ratio case -- Carnahan-Starling
+EOS (a = 1, b = 4, R = 1) at T/Tc = 0.5, tau = 0.6, geometric wetting, 64
+seeded droplets (32 per wall), 5000 steps -- in FP32 with the fused kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+* value: MLUPS over fluid nodes, state resident in HBM, K steps timed with
+  CUDA events on the solver's stream (max over ranks; N > 1 runs one
+  independent replica per GPU, weak scaling, no collective on the data path).
+* e2e: the same metric through the C ABI with host buffers: upload of the
+  initial density field from pinned memory, K steps, download of the final
+  density field, all inside the timed region.
+* roofline: the fused step kernel against the measured HBM copy bandwidth;
+  algorithmic bytes = 72 B per fluid node (9 float loads + 9 float stores).
+* cpu_baseline / --impl reference: the FP64 CPU oracle (single thread) on a
+  bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 pseudo-potential MLUPS & % HBM roofline; batched/adjoint vs plain"
+BYTES_PER_NODE = 72  # FP32: 9 loads + 9 stores of the distribution functions
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "fused_step_4096x2048_traffic.json")
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, out_path: str):
+        self.gpu, self.path, self.proc = gpu_index, out_path, None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("", "[N/A]") else 0.0,
+                             parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(loaded)}
+
+
+def _workload():
+    from paper_1501_05430_gb300 import inputs as I
+
+    return I.throughput()
+
+
+def _params(L, w, check_every=0):
+    r = w.rates
+    return L.lbm_params_default(precision=32, kernel=L.LBM_KERNEL_AUTO, check_every=check_every,
+                                s_e=r.get("s_e", 0.0), s_eps=r.get("s_eps", 0.0), s_j=r.get("s_j", 0.0),
+                                s_q=r.get("s_q", 0.0))
+
+
+def cpu_oracle_rate(w, T, rho_v, rho_l, budget_nodes_steps: float, steps_cap: int = 3):
+    """Oracle MLUPS on a bounded sample: the lower-left crop of the workload
+    (both walls kept) with about budget_nodes_steps node-updates."""
+    import oracle as O
+
+    oeos = O.carnahan_starling()
+    rm = O.rho_max(oeos, T, rho_l)
+    inv = 1.0 / w.tau
+    r = dict(s_rho=0.0, s_e=w.rates.get("s_e", inv), s_eps=w.rates.get("s_eps", inv), s_j=w.rates.get("s_j", inv),
+             s_q=w.rates.get("s_q", inv), s_nu=inv)
+    full = w.nx * (w.ny - 2)
+    if budget_nodes_steps >= full * steps_cap:
+        nx, ny, steps = w.nx, w.ny, steps_cap
+    else:
+        steps = 1
+        frac = max(budget_nodes_steps / full, 1e-4)
+        nx = max(64, int(w.nx * np.sqrt(frac)) // 4 * 4)
+        ny = max(16, int(w.ny * np.sqrt(frac)))
+    from paper_1501_05430_gb300 import inputs as I
+
+    rho = I.droplet_field(w.nx, w.ny, w.droplets, rho_v, rho_l, w.width)
+    crop = np.ascontiguousarray(rho[:ny, :nx])
+    crop[-1] = rho[-1, :nx]
+    sim = O.Sim(nx, ny, oeos, T, tau=w.tau, theta=np.ascontiguousarray(w.theta[:ny, :nx]), rates=r, rho_max_=rm)
+    sim.set_rho(crop)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    sim.close()
+    return nx * (ny - 2) * steps / dt / 1e6, f"{nx}x{ny} crop of the workload, {steps} step(s)", nx, ny, steps
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1501_05430_gb300 import lbm as L  # host-side set-up only (no GPU use)
+
+    w = _workload()
+    eos = L.carnahan_starling()
+    T = w.t_over_tc * L.lbm_eos_critical(eos)[0]
+    rv, rl = L.lbm_coexistence(eos, T)
+    # each step: one oracle step on a crop sized so the whole run ends in ~2 minutes
+    per_step = 2.5e6 * 100.0 / max(1, args.steps + args.warmup)
+    import oracle as O
+
+    oeos = O.carnahan_starling()
+    rm = O.rho_max(oeos, T, rl)
+    inv = 1.0 / w.tau
+    r = dict(s_rho=0.0, s_e=w.rates.get("s_e", inv), s_eps=w.rates.get("s_eps", inv), s_j=w.rates.get("s_j", inv),
+             s_q=w.rates.get("s_q", inv), s_nu=inv)
+    frac = min(1.0, per_step / (w.nx * (w.ny - 2)))
+    nx = max(64, min(w.nx, int(w.nx * np.sqrt(frac)) // 4 * 4))
+    ny = max(16, min(w.ny, int(w.ny * np.sqrt(frac))))
+    from paper_1501_05430_gb300 import inputs as I
+
+    rho = I.droplet_field(w.nx, w.ny, w.droplets, rv, rl, w.width)
+    crop = np.ascontiguousarray(rho[:ny, :nx])
+    sim = O.Sim(nx, ny, oeos, T, tau=w.tau, theta=np.ascontiguousarray(w.theta[:ny, :nx]), rates=r, rho_max_=rm)
+    sim.set_rho(crop)
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    st = sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = nx * (ny - 2) * args.steps / dt / 1e6
+    sample = f"{nx}x{ny} crop of {w.name} (both walls, its droplets and angles), {args.steps} steps"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "sample": sample, "oracle_status": st},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1501_05430_gb300 import inputs as I
+    from paper_1501_05430_gb300 import lbm as L
+
+    L.load()
+    w = _workload()
+    eos = L.carnahan_starling()
+    T = w.t_over_tc * L.lbm_eos_critical(eos)[0]
+    rv, rl = L.lbm_coexistence(eos, T)
+    rho0 = I.droplet_field(w.nx, w.ny, w.droplets, rv, rl, w.width)
+    stream = torch.cuda.Stream()
+    params = _params(L, w)
+    sim = L.Lbm(w.nx, w.ny, eos, T, w.tau, theta=w.theta, params=params, stream=stream)
+    info = sim.info
+    sim.set_rho(rho0)
+    sim.step(args.warmup)
+    sim.sync()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing -------------------------------------------
+    clocks = ClockSampler(local, os.path.join(tempfile.gettempdir(), f"lbm_clocks_{os.getpid()}.csv"))
+    clocks.start()
+    barrier()
+    launches0 = sim.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    barrier()
+    launches = sim.launches() - launches0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    status = sim.status()
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    fluid = w.nx * (w.ny - 2)
+    value = ws * fluid * args.steps / (t_max * 1e-3) / 1e6
+    kernel_ms = ms / max(1, launches) if info.kernel_in_use == L.LBM_KERNEL_FUSED else None
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    pinned_in = torch.empty((w.ny, w.nx), dtype=torch.float64, pin_memory=True).numpy()
+    pinned_in[:] = rho0
+    pinned_out = torch.empty((w.ny, w.nx), dtype=torch.float64, pin_memory=True).numpy()
+    barrier()
+    t0 = time.perf_counter()
+    sim.set_rho(pinned_in)
+    sim.step(args.steps)
+    L.lbm_get_rho(sim.ctx, pinned_out)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = ws * fluid * args.steps / e2e_s / 1e6
+    node_bytes = 8 * w.nx * w.ny
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        traffic = None
+        try:
+            with open(PROFILE_TRAFFIC) as fh:
+                tr = json.load(fh)
+            if tr.get("nx") == w.nx and tr.get("ny") == w.ny and tr.get("kernel_sha") == _kernel_sha():
+                traffic = tr["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+        roof = None
+        if kernel_ms:
+            achieved = BYTES_PER_NODE * fluid / (kernel_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "peak_source": peak_kind, "kernel": "k_fused (fused FP32 step)",
+                    "algorithmic_bytes_per_launch": BYTES_PER_NODE * fluid}
+        cpu = None
+        if ws == 1 and not args.no_cpu:
+            v, sample, *_ = cpu_oracle_rate(w, T, rv, rl, budget_nodes_steps=2.5e7)
+            cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "fluid_nodes": fluid,
+                       "eos": "Carnahan-Starling a=1 b=4 R=1", "T_over_Tc": w.t_over_tc, "tau": w.tau,
+                       "wetting": "geometric (Eqs. 19-21, 4 iterations)", "droplets": len(w.droplets),
+                       "kernel": "fused" if info.kernel_in_use == L.LBM_KERNEL_FUSED else "reference",
+                       "tile": {"w": info.tile_w, "blocks": info.tile_blocks, "stages": info.tile_stages},
+                       "l2": "inputs larger than L2 (2 x 302 MB distribution arrays per step)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "stable_after_run": status == 0, "notes": w.notes},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": node_bytes / args.steps,
+                    "d2h_bytes_per_step": node_bytes / args.steps,
+                    "what": "lbm_set_rho from pinned host memory + K x lbm_step + lbm_get_rho to pinned host memory"},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _kernel_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1501_05430_gb300", "csrc", "lbm_fused.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -537,7 +537,11 @@ static void orc_fields(orc_sim *S) {
                            S->rho[IDX(S, y1, x)], S->rho[IDX(S, y2, x)], c[x], cot[x], S->n_iter,
                            S->rho_max);
       double p, u;
-      orc_psi_U(S->kind, S->eos, S->T, g, &p, &u);
+      /* rho_max is the root of U = p - rho/3 (Eq. 10), so psi = U = 0 there
+       * by definition; evaluating the EOS at the root would only return the
+       * square root of a rounding residue. */
+      if (g >= S->rho_max) { p = 0.0; u = 0.0; }
+      else orc_psi_U(S->kind, S->eos, S->T, g, &p, &u);
       S->rho[IDX(S, yg, x)] = g;
       S->psi[IDX(S, yg, x)] = p;
       S->U[IDX(S, yg, x)] = u;

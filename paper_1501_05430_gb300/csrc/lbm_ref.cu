@@ -1,0 +1,429 @@
+// lbm_ref.cu -- unfused reference kernels of the pseudo-potential D2Q9 step,
+// written in the canonical evaluation order (sums left to right in index
+// order, integer moment coefficients applied as multiplications) and compiled
+// with -fmad=false, so that the double instantiation is bit-identical to any
+// IEEE FP64 evaluation of the step in the same order.
+//
+// One step = lbm_ref_fields (rho, psi, U; Eqs. 1, 10, 11) -> lbm_ref_ghost
+// (Eqs. 19-21 or the Martys-Chen zero potential) -> lbm_ref_collide (Eq. 9
+// [+ Eq. 14], Eqs. 16-17, collision Eqs. 4-6 and 15, streaming of Eq. 1 with
+// half-way bounce-back).  The fused FP32 kernel (lbm_fused.cu) computes the
+// same step in one pass; these kernels also serve the macroscopic getters.
+#include <math.h>
+
+#include "lbm_internal.h"
+
+namespace {
+
+// D2Q9 velocities, opposite directions, the moment basis (rho, e, eps, jx, qx,
+// jy, qy, pxx, pxy) and its row norms.  Kept as local tables so that fully
+// unrolled loops fold every coefficient into the instruction stream.
+__device__ __forceinline__ int EX(int a) {
+  const int t[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  return t[a];
+}
+__device__ __forceinline__ int EY(int a) {
+  const int t[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  return t[a];
+}
+__device__ __forceinline__ int OPP(int a) {
+  const int t[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  return t[a];
+}
+__device__ __forceinline__ double MC(int k, int a) {
+  const double t[9][9] = {
+      {1, 1, 1, 1, 1, 1, 1, 1, 1},     {-4, -1, -1, -1, -1, 2, 2, 2, 2}, {4, -2, -2, -2, -2, 1, 1, 1, 1},
+      {0, 1, 0, -1, 0, 1, -1, -1, 1},  {0, -2, 0, 2, 0, 1, -1, -1, 1},   {0, 0, 1, 0, -1, 1, 1, -1, -1},
+      {0, 0, -2, 0, 2, 1, 1, -1, -1},  {0, 1, -1, 1, -1, 0, 0, 0, 0},    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+  return t[k][a];
+}
+__device__ __forceinline__ double NRM(int k) {
+  const double t[9] = {9, 36, 36, 6, 12, 6, 12, 4, 4};
+  return t[k];
+}
+
+template <typename R>
+struct Mdl {
+  int nx, ny, walls, kind, n_iter, wetting;
+  R a, b, Rg, T, thv, thm, thl, r1, r2, A, kappa, Gw, rho_max;
+  R s[9];
+  __device__ explicit Mdl(const lbm_dev_params &P)
+      : nx(P.nx), ny(P.ny), walls(P.walls), kind(P.eos_kind), n_iter(P.n_iter), wetting(P.wetting),
+        a((R)P.a), b((R)P.b), Rg((R)P.R), T((R)P.T), thv((R)P.thv), thm((R)P.thm), thl((R)P.thl),
+        r1((R)P.r1), r2((R)P.r2), A((R)P.A), kappa((R)P.kappa), Gw((R)P.Gw), rho_max((R)P.rho_max) {
+    for (int k = 0; k < 9; ++k) s[k] = (R)P.s[k];
+  }
+  __device__ bool solid_row(int y) const { return walls && (y == 0 || y == ny - 1); }
+  __device__ int wx(int x) const { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+  __device__ int wy(int y) const { return y < 0 ? y + ny : (y >= ny ? y - ny : y); }
+};
+
+// Carnahan-Starling or Eq. 11 pressure.
+template <typename R>
+__device__ R pressure(const Mdl<R> &m, R rho) {
+  if (m.kind == LBM_EOS_CARNAHAN_STARLING) {
+    R eta = (m.b * rho) * (R)0.25;
+    R num = (((R)1 + eta) + eta * eta) - (eta * eta) * eta;
+    R den = (((R)1 - eta) * ((R)1 - eta)) * ((R)1 - eta);
+    return (((rho * m.Rg) * m.T) * num) / den - (m.a * rho) * rho;
+  }
+  if (rho <= m.r1) return rho * m.thv;
+  if (rho <= m.r2) return m.r1 * m.thv + (rho - m.r1) * m.thm;
+  return (m.r1 * m.thv + (m.r2 - m.r1) * m.thm) + (rho - m.r2) * m.thl;
+}
+
+// Eq. 10 with c = 1, G = -1: U = p - rho/3, psi = sqrt(max(0, -2U)).
+template <typename R>
+__device__ void psi_U(const Mdl<R> &m, R rho, R &psi, R &U) {
+  R u = pressure(m, rho) - rho / (R)3;
+  U = u;
+  psi = sqrt(fmax((R)0, (R)-2 * u));
+}
+
+template <typename R>
+__device__ __forceinline__ R wgt(int a) { return a <= 4 ? (R)1 / (R)3 : (R)1 / (R)12; }
+
+template <typename R>
+__global__ void k_fields(lbm_dev_params P, const R *__restrict__ f, R *__restrict__ fields, int *flag) {
+  Mdl<R> m(P);
+  size_t n = (size_t)m.nx * m.ny;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int y = (int)(i / m.nx);
+  if (m.solid_row(y)) return;
+  R r = (R)0;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) r = r + f[a * n + i];
+  R psi, U;
+  psi_U(m, r, psi, U);
+  fields[i] = r;
+  fields[n + i] = psi;
+  fields[2 * n + i] = U;
+  if (!(r > (R)0) || r > m.rho_max) atomicOr(flag, 1);
+}
+
+// Eqs. 19-21 (geometric) or zero potential (Martys-Chen) on the solid rows.
+template <typename R>
+__global__ void k_ghost(lbm_dev_params P, const double *__restrict__ coef, R *__restrict__ fields) {
+  Mdl<R> m(P);
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * m.nx) return;
+  int w = t / m.nx, x = t - w * m.nx;
+  size_t n = (size_t)m.nx * m.ny;
+  int yg = w == 0 ? 0 : m.ny - 1, y1 = w == 0 ? 1 : m.ny - 2, y2 = w == 0 ? 2 : m.ny - 3;
+  size_t ig = (size_t)yg * m.nx + x;
+  if (m.wetting == LBM_WET_MARTYS_CHEN) {
+    fields[ig] = (R)0;
+    fields[n + ig] = (R)0;
+    fields[2 * n + ig] = (R)0;
+    return;
+  }
+  const R *rho = fields;
+  R rim1 = rho[(size_t)y1 * m.nx + m.wx(x - 1)];
+  R rip1 = rho[(size_t)y1 * m.nx + m.wx(x + 1)];
+  R ri1 = rho[(size_t)y1 * m.nx + x];
+  R ri2 = rho[(size_t)y2 * m.nx + x];
+  R c = (R)coef[w * m.nx + x];
+  R cot = (R)coef[2 * m.nx + w * m.nx + x];
+  R a = rip1 - rim1;
+  R g;
+  if (m.n_iter <= 0) {
+    g = ri2 + cot * fabs(a);
+  } else {
+    R d = (R)2 * (ri2 - ri1);
+    g = ri2;
+    for (int k = 0; k < m.n_iter; ++k) {
+      R s = a * a + d * d;
+      g = ri2 + c * sqrt(s);
+      d = ri2 - g;
+    }
+  }
+  g = fmin(fmax(g, (R)0), m.rho_max);
+  // at the clamp rho_max (the root of U, Eq. 10) psi and U take their exact value 0
+  R psi = (R)0, U = (R)0;
+  if (g < m.rho_max) psi_U(m, g, psi, U);
+  fields[ig] = g;
+  fields[n + ig] = psi;
+  fields[2 * n + ig] = U;
+}
+
+// Eq. 9 force (+ Eq. 14) and Eq. 17 tensor at fluid node (x, y).
+template <typename R>
+__device__ void force_Q(const Mdl<R> &m, const R *__restrict__ fields, int y, int x, R &Fx, R &Fy, R &Qxx,
+                        R &Qyy, R &Qxy) {
+  size_t n = (size_t)m.nx * m.ny;
+  const R *psi = fields + n, *U = fields + 2 * n;
+  R psi0 = psi[(size_t)y * m.nx + x];
+  R spx = 0, spy = 0, sUx = 0, sUy = 0, ssx = 0, ssy = 0;
+  R qxx1 = 0, qyy1 = 0, qxy1 = 0, qxx2 = 0, qyy2 = 0, qxy2 = 0;
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    int yn = m.wy(y + EY(a)), xn = m.wx(x + EX(a));
+    size_t j = (size_t)yn * m.nx + xn;
+    R pn = psi[j], un = U[j];
+    R w = wgt<R>(a);
+    R solid = m.solid_row(yn) ? (R)1 : (R)0;
+    if (EX(a) != 0) {
+      R tp = w * pn, tu = w * un, ts = w * solid;
+      if (EX(a) > 0) { spx = spx + tp; sUx = sUx + tu; ssx = ssx + ts; }
+      else { spx = spx - tp; sUx = sUx - tu; ssx = ssx - ts; }
+    }
+    if (EY(a) != 0) {
+      R tp = w * pn, tu = w * un, ts = w * solid;
+      if (EY(a) > 0) { spy = spy + tp; sUy = sUy + tu; ssy = ssy + ts; }
+      else { spy = spy - tp; sUy = sUy - tu; ssy = ssy - ts; }
+    }
+    R t1 = w * (pn - psi0);
+    R t2 = w * (pn * pn - psi0 * psi0);
+    int exx = EX(a) * EX(a), eyy = EY(a) * EY(a), exy = EX(a) * EY(a);
+    if (exx) { qxx1 = qxx1 + t1; qxx2 = qxx2 + t2; }
+    if (eyy) { qyy1 = qyy1 + t1; qyy2 = qyy2 + t2; }
+    if (exy > 0) { qxy1 = qxy1 + t1; qxy2 = qxy2 + t2; }
+    if (exy < 0) { qxy1 = qxy1 - t1; qxy2 = qxy2 - t2; }
+  }
+  const R G = (R)-1;
+  R cpsi = (((R)1 - m.A) * G) * psi0;
+  R fx = -(m.A * sUx) - cpsi * spx;
+  R fy = -(m.A * sUy) - cpsi * spy;
+  if (m.wetting == LBM_WET_MARTYS_CHEN) {
+    R gp = m.Gw * psi0;
+    fx = fx + (-(gp * ssx));
+    fy = fy + (-(gp * ssy));
+  }
+  R pre = m.kappa * (G * (R)0.5);
+  R c1 = ((R)1 - m.A) * psi0, c2 = m.A * (R)0.5;
+  Fx = fx;
+  Fy = fy;
+  Qxx = pre * ((c1 * qxx1) + (c2 * qxx2));
+  Qyy = pre * ((c1 * qyy1) + (c2 * qyy2));
+  Qxy = pre * ((c1 * qxy1) + (c2 * qxy2));
+}
+
+// MRT collision with forcing (Eqs. 4, 6, 15 with the Eq. 16 source).
+template <typename R>
+__device__ void collide(const Mdl<R> &m, const R *f, R rho, R Fx, R Fy, R Qxx, R Qyy, R Qxy, R *fs) {
+  R mm[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    R acc = (R)0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a)
+      if (MC(k, a) != 0.0) acc = acc + (R)MC(k, a) * f[a];
+    mm[k] = acc;
+  }
+  R vx = (mm[3] + (R)0.5 * Fx) / rho;
+  R vy = (mm[5] + (R)0.5 * Fy) / rho;
+  R v2 = vx * vx + vy * vy;
+  R meq[9], S[9], C[9];
+  meq[0] = rho;
+  meq[1] = rho * ((R)-2 + (R)3 * v2);
+  meq[2] = rho * ((R)1 - (R)3 * v2);
+  meq[3] = rho * vx;
+  meq[4] = -(rho * vx);
+  meq[5] = rho * vy;
+  meq[6] = -(rho * vy);
+  meq[7] = rho * (vx * vx - vy * vy);
+  meq[8] = rho * (vx * vy);
+  R vF = vx * Fx + vy * Fy;
+  S[0] = 0;
+  S[1] = (R)6 * vF;
+  S[2] = -((R)6 * vF);
+  S[3] = Fx;
+  S[4] = -Fx;
+  S[5] = Fy;
+  S[6] = -Fy;
+  S[7] = (R)2 * (vx * Fx - vy * Fy);
+  S[8] = vx * Fy + vy * Fx;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) C[k] = 0;
+  C[1] = ((R)1.5 * m.s[1]) * (Qxx + Qyy);
+  C[7] = -(m.s[7] * (Qxx - Qyy));
+  C[8] = -(m.s[8] * Qxy);
+  R r[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    R ms = ((mm[k] - m.s[k] * (mm[k] - meq[k])) + ((R)1 - (R)0.5 * m.s[k]) * S[k]) + C[k];
+    r[k] = ms / (R)NRM(k);
+  }
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    R acc = (R)0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      if (MC(k, a) != 0.0) acc = acc + (R)MC(k, a) * r[k];
+    fs[a] = acc;
+  }
+}
+
+template <typename R>
+__global__ void k_collide(lbm_dev_params P, const R *__restrict__ fin, R *__restrict__ fout,
+                          const R *__restrict__ fields) {
+  Mdl<R> m(P);
+  size_t n = (size_t)m.nx * m.ny;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int y = (int)(i / m.nx), x = (int)(i - (size_t)y * m.nx);
+  if (m.solid_row(y)) return;
+  R Fx, Fy, Qxx, Qyy, Qxy;
+  force_Q(m, fields, y, x, Fx, Fy, Qxx, Qyy, Qxy);
+  R fl[9], fs[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) fl[a] = fin[a * n + i];
+  collide(m, fl, fields[i], Fx, Fy, Qxx, Qyy, Qxy, fs);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    int yt = m.wy(y + EY(a));
+    if (m.solid_row(yt)) {
+      fout[OPP(a) * n + i] = fs[a];
+    } else {
+      fout[a * n + (size_t)yt * m.nx + m.wx(x + EX(a))] = fs[a];
+    }
+  }
+}
+
+// Macroscopic outputs at every node: out7 = {ux, uy, Fx, Fy, Qxx, Qyy, Qxy}
+// (zero on the solid rows).
+template <typename R>
+__global__ void k_macro(lbm_dev_params P, const R *__restrict__ f, const R *__restrict__ fields,
+                        double *__restrict__ out7) {
+  Mdl<R> m(P);
+  size_t n = (size_t)m.nx * m.ny;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int y = (int)(i / m.nx), x = (int)(i - (size_t)y * m.nx);
+  if (m.solid_row(y)) {
+    for (int k = 0; k < 7; ++k) out7[k * n + i] = 0.0;
+    return;
+  }
+  R Fx, Fy, Qxx, Qyy, Qxy;
+  force_Q(m, fields, y, x, Fx, Fy, Qxx, Qyy, Qxy);
+  R jx = 0, jy = 0;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    if (MC(3, a) != 0.0) jx = jx + (R)MC(3, a) * f[a * n + i];
+    if (MC(5, a) != 0.0) jy = jy + (R)MC(5, a) * f[a * n + i];
+  }
+  R r = fields[i];
+  out7[i] = (double)((jx + (R)0.5 * Fx) / r);
+  out7[n + i] = (double)((jy + (R)0.5 * Fy) / r);
+  out7[2 * n + i] = (double)Fx;
+  out7[3 * n + i] = (double)Fy;
+  out7[4 * n + i] = (double)Qxx;
+  out7[5 * n + i] = (double)Qyy;
+  out7[6 * n + i] = (double)Qxy;
+}
+
+// f := M^-1 m_eq(rho, 0), evaluated in double in the canonical order.
+template <typename R>
+__global__ void k_set_rho(lbm_dev_params P, const double *__restrict__ rho, R *__restrict__ f) {
+  size_t n = (size_t)P.nx * P.ny;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int y = (int)(i / P.nx);
+  if (P.walls && (y == 0 || y == P.ny - 1)) {
+    for (int a = 0; a < 9; ++a) f[a * n + i] = (R)0;
+    return;
+  }
+  double r = rho[i], vx = 0.0, vy = 0.0;
+  double v2 = vx * vx + vy * vy;
+  double meq[9] = {r, r * (-2.0 + 3.0 * v2), r * (1.0 - 3.0 * v2), r * vx, -(r * vx),
+                   r * vy, -(r * vy), r * (vx * vx - vy * vy), r * (vx * vy)};
+  double q[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) q[k] = meq[k] / NRM(k);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      if (MC(k, a) != 0.0) acc = acc + MC(k, a) * q[k];
+    f[a * n + i] = (R)acc;
+  }
+}
+
+// Droplet density field: max over droplets of the tanh profile.
+__global__ void k_droplets(lbm_dev_params P, int nd, const double *__restrict__ drop, double width, double rho_v,
+                           double rho_l, double *__restrict__ rho) {
+  size_t n = (size_t)P.nx * P.ny;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int y = (int)(i / P.nx), x = (int)(i - (size_t)y * P.nx);
+  double best = rho_v;
+  for (int k = 0; k < nd; ++k) {
+    double xc = drop[3 * k], R0 = drop[3 * k + 1];
+    double yc = drop[3 * k + 2] == 0.0 ? 1.0 : (double)(P.ny - 2);
+    double dx = (double)x - xc;
+    double half = 0.5 * P.nx;
+    dx = dx - P.nx * floor((dx + half) / P.nx);
+    double r = sqrt(dx * dx + ((double)y - yc) * ((double)y - yc));
+    double v = 0.5 * (rho_l + rho_v) - 0.5 * (rho_l - rho_v) * tanh(2.0 * (r - R0) / width);
+    best = fmax(best, v);
+  }
+  rho[i] = best;
+}
+
+inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t lbm_ref_fields(const lbm_ctx *C, const void *f, void *fields, unsigned long long *launches) {
+  size_t n = (size_t)C->nx * C->ny;
+  if (C->precision == 64)
+    k_fields<double><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, (const double *)f, (double *)fields, C->d_flag);
+  else
+    k_fields<float><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, (const float *)f, (float *)fields, C->d_flag);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t lbm_ref_ghost(const lbm_ctx *C, void *fields, unsigned long long *launches) {
+  if (!C->walls) return cudaSuccess;
+  if (C->precision == 64)
+    k_ghost<double><<<nblk(2 * C->nx, 128), 128, 0, C->stream>>>(C->dp, C->d_coef, (double *)fields);
+  else
+    k_ghost<float><<<nblk(2 * C->nx, 128), 128, 0, C->stream>>>(C->dp, C->d_coef, (float *)fields);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t lbm_ref_collide(const lbm_ctx *C, const void *fin, void *fout, const void *fields,
+                            unsigned long long *launches) {
+  size_t n = (size_t)C->nx * C->ny;
+  if (C->precision == 64)
+    k_collide<double><<<nblk(n, 128), 128, 0, C->stream>>>(C->dp, (const double *)fin, (double *)fout,
+                                                           (const double *)fields);
+  else
+    k_collide<float><<<nblk(n, 128), 128, 0, C->stream>>>(C->dp, (const float *)fin, (float *)fout,
+                                                          (const float *)fields);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t lbm_ref_macro(const lbm_ctx *C, const void *f, const void *fields, double *out7,
+                          unsigned long long *launches) {
+  size_t n = (size_t)C->nx * C->ny;
+  if (C->precision == 64)
+    k_macro<double><<<nblk(n, 128), 128, 0, C->stream>>>(C->dp, (const double *)f, (const double *)fields, out7);
+  else
+    k_macro<float><<<nblk(n, 128), 128, 0, C->stream>>>(C->dp, (const float *)f, (const float *)fields, out7);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t lbm_ref_set_rho(const lbm_ctx *C, const double *rho, void *f, unsigned long long *launches) {
+  size_t n = (size_t)C->nx * C->ny;
+  if (C->precision == 64)
+    k_set_rho<double><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, rho, (double *)f);
+  else
+    k_set_rho<float><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, rho, (float *)f);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t lbm_ref_droplets(const lbm_ctx *C, int nd, const double *drop, double width, double *rho,
+                             unsigned long long *launches) {
+  size_t n = (size_t)C->nx * C->ny;
+  k_droplets<<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, nd, drop, width, C->rho_v, C->rho_l, rho);
+  ++*launches;
+  return cudaGetLastError();
+}

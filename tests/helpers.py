@@ -1,0 +1,82 @@
+"""Test helpers: build an oracle simulation and a liblbm context with the
+same parameters, from the seeded workloads of paper_1501_05430_gb300.inputs."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+from paper_1501_05430_gb300 import inputs as I
+from paper_1501_05430_gb300 import lbm as L
+
+BIG = np.finfo(np.float64).max
+
+
+def cs_T(t_over_tc: float, a=1.0, b=4.0, R=1.0) -> float:
+    tc, _ = O.cs_critical(O.carnahan_starling(a, b, R))
+    return t_over_tc * tc
+
+
+def resolve_rates(tau, rates=None):
+    inv = 1.0 / tau
+    r = dict(s_rho=0.0, s_e=inv, s_eps=inv, s_j=inv, s_q=inv, s_nu=inv)
+    for k, v in (rates or {}).items():
+        if v:
+            r[k] = v
+    return r
+
+
+class Pair:
+    """An oracle Sim and a GPU context with identical inputs."""
+
+    def __init__(self, nx, ny, *, t_over_tc=0.8, tau=1.0, eos="cs", pw=None, theta=np.pi / 2, walls=True,
+                 A=-0.6, kappa=0.5, G_w=0.0, n_iter=4, wetting=0, rates=None, precision=64,
+                 kernel=L.LBM_KERNEL_AUTO, check_every=0, torch_state=False, stream=None):
+        self.nx, self.ny = nx, ny
+        if eos == "cs":
+            self.oeos = O.carnahan_starling()
+            self.geos = L.carnahan_starling()
+            self.T = cs_T(t_over_tc)
+            self.rho_v, self.rho_l = O.coexistence(self.oeos, self.T)
+        else:
+            tv, tm, tl, r1, r2 = pw
+            self.oeos = O.piecewise(tv, tm, tl, r1, r2)
+            self.geos = L.piecewise(tv, tm, tl, r1, r2)
+            self.T = 0.0
+            self.rho_v, self.rho_l = O.coexistence(self.oeos)
+        self.rho_max = O.rho_max(self.oeos, self.T, self.rho_l)
+        self.rho_mid = 0.5 * (self.rho_v + self.rho_l)
+        r = resolve_rates(tau, rates)
+        theta = np.broadcast_to(np.asarray(theta, dtype=float), (ny, nx)).copy()
+        self.theta = theta
+        self.orc = O.Sim(nx, ny, self.oeos, self.T, tau=tau, walls=walls, A=A, kappa=kappa, G_w=G_w,
+                         n_iter=n_iter, wetting=wetting, theta=theta, rates=r, rho_max_=self.rho_max)
+        p = L.lbm_params_default(A=A, kappa=kappa, G_w=G_w, n_iter=n_iter, wetting=wetting, precision=precision,
+                                 kernel=kernel, s_e=r["s_e"], s_eps=r["s_eps"], s_j=r["s_j"], s_q=r["s_q"],
+                                 s_nu=r["s_nu"], check_every=check_every, rho_max=min(self.rho_max, 1e300),
+                                 rho_mid=self.rho_mid)
+        self.gpu = L.Lbm(nx, ny, self.geos, self.T, tau, theta=theta, walls=walls, params=p, stream=stream,
+                         torch_state=torch_state)
+
+    def set_rho(self, rho):
+        self.orc.set_rho(rho)
+        self.gpu.set_rho(rho)
+
+    def set_f(self, f):
+        self.orc.set_f(f)
+        self.gpu.set_f(f)
+
+    def step(self, n):
+        so = self.orc.step(n)
+        self.gpu.step(n)
+        return so
+
+    def close(self):
+        self.gpu.close()
+        self.orc.close()
+
+
+def droplet_pair(w: I.Workload, precision=64, kernel=L.LBM_KERNEL_AUTO, **kw) -> Pair:
+    p = Pair(w.nx, w.ny, t_over_tc=w.t_over_tc, tau=w.tau, theta=w.theta, rates=w.rates, precision=precision,
+             kernel=kernel, **kw)
+    p.set_rho(I.droplet_field(w.nx, w.ny, w.droplets, p.rho_v, p.rho_l, w.width))
+    return p

@@ -107,3 +107,21 @@ def test_clamp_to_valid_range():
     assert O.ghost(0.0, 1.0, 0.01, 0.02, c, cot, 4, 0.55) == 0.0
     c, cot = _coeffs(math.radians(5))
     assert O.ghost(0.0, 1.0, 0.01, 0.5, c, cot, 4, 0.55) == 0.55
+
+
+def test_clamped_ghost_carries_zero_potential():
+    """A ghost density clamped at rho_max (the root of U = p - rho/3, Eq. 10)
+    carries psi = U = 0 exactly in the simulation fields."""
+    eos = O.carnahan_starling()
+    T = 0.5 * O.cs_critical(eos)[0]
+    rv, rl = O.coexistence(eos, T)
+    rm = O.rho_max(eos, T, rl)
+    nx, ny = 12, 8
+    s = O.Sim(nx, ny, eos, T, tau=0.6, theta=math.radians(20.0), rho_max_=rm)
+    rho = np.full((ny, nx), rl)
+    rho[1, 6:] = rv  # sharp step on the boundary row: large tangential gradient
+    s.set_rho(rho)
+    fl = s.fields()
+    clamped = fl["rho"][0] == rm
+    assert clamped.any()
+    assert np.all(fl["psi"][0][clamped] == 0.0) and np.all(fl["U"][0][clamped] == 0.0)
