@@ -1,8 +1,9 @@
 """Throughput benchmark of the pseudo-potential D2Q9 step (one JSON line).
 
-Default workload: the 4096 x 2048 large-density-ratio case -- Carnahan-Starling
-EOS (a = 1, b = 4, R = 1) at T/Tc = 0.5, tau = 0.6, geometric wetting, 64
-seeded droplets (32 per wall), 5000 steps -- in FP32 with the fused kernel.
+Default workload: the 4096 x 2048 large-density-ratio case -- the Eq. 11 EOS of
+Table 1 at density ratio 1000, the paper's relaxation (all rates 1), geometric
+wetting with 4 iterations, 64 seeded droplets (32 per wall, theta ~ U[30, 150]
+deg), 5000 steps -- in FP32 with the fused kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -105,25 +106,62 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(loaded)}
 
 
+_SIZE = {}
+
+
 def _workload():
+    """The 4096 x 2048 throughput workload, or the same recipe at the size
+    given by --nx/--ny (used for short profiler captures)."""
     from paper_1501_05430_gb300 import inputs as I
 
-    return I.throughput()
+    return I.throughput(**_SIZE)
 
 
 def _params(L, w, check_every=0):
     r = w.rates
-    return L.lbm_params_default(precision=32, kernel=L.LBM_KERNEL_AUTO, check_every=check_every,
-                                s_e=r.get("s_e", 0.0), s_eps=r.get("s_eps", 0.0), s_j=r.get("s_j", 0.0),
-                                s_q=r.get("s_q", 0.0))
+    return L.lbm_params_default(precision=32, kernel=L.LBM_KERNEL_AUTO, check_every=check_every, A=w.A,
+                                kappa=w.kappa, s_e=r.get("s_e", 0.0), s_eps=r.get("s_eps", 0.0),
+                                s_j=r.get("s_j", 0.0), s_q=r.get("s_q", 0.0))
 
 
-def cpu_oracle_rate(w, T, rho_v, rho_l, budget_nodes_steps: float, steps_cap: int = 3):
+def _lib_eos(L, w):
+    """(lbm_eos, T) of a workload for the library."""
+    e = w.eos
+    if e["kind"] == "cs":
+        eos = L.carnahan_starling(e["a"], e["b"], e["R"])
+        return eos, w.t_over_tc * L.lbm_eos_critical(eos)[0]
+    return L.piecewise(e["theta_v"], e["theta_m"], e["theta_l"], e["rho1"], e["rho2"]), 0.0
+
+
+def _oracle_eos(O, w):
+    e = w.eos
+    if e["kind"] == "cs":
+        return O.carnahan_starling(e["a"], e["b"], e["R"])
+    return O.piecewise(e["theta_v"], e["theta_m"], e["theta_l"], e["rho1"], e["rho2"])
+
+
+def _eos_desc(w):
+    e = w.eos
+    if e["kind"] == "cs":
+        return f"Carnahan-Starling a={e['a']} b={e['b']} R={e['R']}, T/Tc={w.t_over_tc}"
+    return (f"Eq. 11 piecewise (Table 1, ratio 1000): rho1={e['rho1']} rho2={e['rho2']} "
+            f"theta_v={e['theta_v']} theta_m={e['theta_m']} theta_l={e['theta_l']}")
+
+
+def _oracle_setup(O, w):
+    """Oracle-side EOS, temperature and coexistence densities of a workload."""
+    oeos = _oracle_eos(O, w)
+    T = w.t_over_tc * O.cs_critical(oeos)[0] if w.eos["kind"] == "cs" else 0.0
+    rho_v, rho_l = O.coexistence(oeos, T)
+    return oeos, T, rho_v, rho_l
+
+
+def cpu_oracle_rate(w, budget_nodes_steps: float, steps_cap: int = 3):
     """Oracle MLUPS on a bounded sample: the lower-left crop of the workload
     (both walls kept) with about budget_nodes_steps node-updates."""
     import oracle as O
 
-    oeos = O.carnahan_starling()
+    oeos, T, rho_v, rho_l = _oracle_setup(O, w)
     rm = O.rho_max(oeos, T, rho_l)
     inv = 1.0 / w.tau
     r = dict(s_rho=0.0, s_e=w.rates.get("s_e", inv), s_eps=w.rates.get("s_eps", inv), s_j=w.rates.get("s_j", inv),
@@ -141,7 +179,8 @@ def cpu_oracle_rate(w, T, rho_v, rho_l, budget_nodes_steps: float, steps_cap: in
     rho = I.droplet_field(w.nx, w.ny, w.droplets, rho_v, rho_l, w.width)
     crop = np.ascontiguousarray(rho[:ny, :nx])
     crop[-1] = rho[-1, :nx]
-    sim = O.Sim(nx, ny, oeos, T, tau=w.tau, theta=np.ascontiguousarray(w.theta[:ny, :nx]), rates=r, rho_max_=rm)
+    sim = O.Sim(nx, ny, oeos, T, tau=w.tau, theta=np.ascontiguousarray(w.theta[:ny, :nx]), rates=r, rho_max_=rm,
+                A=w.A, kappa=w.kappa)
     sim.set_rho(crop)
     t0 = time.perf_counter()
     sim.step(steps)
@@ -154,17 +193,12 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    from paper_1501_05430_gb300 import lbm as L  # host-side set-up only (no GPU use)
-
-    w = _workload()
-    eos = L.carnahan_starling()
-    T = w.t_over_tc * L.lbm_eos_critical(eos)[0]
-    rv, rl = L.lbm_coexistence(eos, T)
-    # each step: one oracle step on a crop sized so the whole run ends in ~2 minutes
-    per_step = 2.5e6 * 100.0 / max(1, args.steps + args.warmup)
     import oracle as O
 
-    oeos = O.carnahan_starling()
+    w = _workload()
+    oeos, T, rv, rl = _oracle_setup(O, w)
+    # each step: one oracle step on a crop sized so the whole run ends in ~2 minutes
+    per_step = 2.5e6 * 100.0 / max(1, args.steps + args.warmup)
     rm = O.rho_max(oeos, T, rl)
     inv = 1.0 / w.tau
     r = dict(s_rho=0.0, s_e=w.rates.get("s_e", inv), s_eps=w.rates.get("s_eps", inv), s_j=w.rates.get("s_j", inv),
@@ -176,7 +210,8 @@ def run_reference(args):
 
     rho = I.droplet_field(w.nx, w.ny, w.droplets, rv, rl, w.width)
     crop = np.ascontiguousarray(rho[:ny, :nx])
-    sim = O.Sim(nx, ny, oeos, T, tau=w.tau, theta=np.ascontiguousarray(w.theta[:ny, :nx]), rates=r, rho_max_=rm)
+    sim = O.Sim(nx, ny, oeos, T, tau=w.tau, theta=np.ascontiguousarray(w.theta[:ny, :nx]), rates=r, rho_max_=rm,
+                A=w.A, kappa=w.kappa)
     sim.set_rho(crop)
     sim.step(args.warmup)
     t0 = time.perf_counter()
@@ -212,8 +247,7 @@ def run_ours(args):
 
     L.load()
     w = _workload()
-    eos = L.carnahan_starling()
-    T = w.t_over_tc * L.lbm_eos_critical(eos)[0]
+    eos, T = _lib_eos(L, w)
     rv, rl = L.lbm_coexistence(eos, T)
     rho0 = I.droplet_field(w.nx, w.ny, w.droplets, rv, rl, w.width)
     stream = torch.cuda.Stream()
@@ -253,16 +287,21 @@ def run_ours(args):
     kernel_ms = ms / max(1, launches) if info.kernel_in_use == L.LBM_KERNEL_FUSED else None
 
     # ---- end to end through the C ABI with host buffers ---------------------
+    # a second context (created outside the timed region) so that the result
+    # does not depend on the state the timed run left behind
+    sim2 = L.Lbm(w.nx, w.ny, eos, T, w.tau, theta=w.theta, params=params, stream=stream)
     pinned_in = torch.empty((w.ny, w.nx), dtype=torch.float64, pin_memory=True).numpy()
     pinned_in[:] = rho0
     pinned_out = torch.empty((w.ny, w.nx), dtype=torch.float64, pin_memory=True).numpy()
+    sim2.sync()
     barrier()
     t0 = time.perf_counter()
-    sim.set_rho(pinned_in)
-    sim.step(args.steps)
-    L.lbm_get_rho(sim.ctx, pinned_out)
+    sim2.set_rho(pinned_in)
+    sim2.step(args.steps)
+    L.lbm_get_rho(sim2.ctx, pinned_out)
     barrier()
     e2e_s = time.perf_counter() - t0
+    sim2.close()
     if ws > 1:
         t = torch.tensor([e2e_s], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -288,14 +327,14 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": BYTES_PER_NODE * fluid}
         cpu = None
         if ws == 1 and not args.no_cpu:
-            v, sample, *_ = cpu_oracle_rate(w, T, rv, rl, budget_nodes_steps=2.5e7)
+            v, sample, *_ = cpu_oracle_rate(w, budget_nodes_steps=2.5e7)
             cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "fluid_nodes": fluid,
-                       "eos": "Carnahan-Starling a=1 b=4 R=1", "T_over_Tc": w.t_over_tc, "tau": w.tau,
+                       "eos": _eos_desc(w), "tau": w.tau, "A": w.A, "kappa": w.kappa,
                        "wetting": "geometric (Eqs. 19-21, 4 iterations)", "droplets": len(w.droplets),
                        "kernel": "fused" if info.kernel_in_use == L.LBM_KERNEL_FUSED else "reference",
                        "tile": {"w": info.tile_w, "blocks": info.tile_blocks, "stages": info.tile_stages},
@@ -333,7 +372,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--nx", type=int, default=None, help="workload width (default 4096)")
+    ap.add_argument("--ny", type=int, default=None, help="workload height (default 2048)")
     args = ap.parse_args()
+    if args.nx:
+        _SIZE["nx"] = args.nx
+    if args.ny:
+        _SIZE["ny"] = args.ny
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

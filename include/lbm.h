@@ -97,8 +97,10 @@ typedef struct lbm_params {
                         inside lbm_step (0 = only when lbm_status is called) */
   double rho_mid;    /* density of the contour used by lbm_contact_angle;
                         0 means (rho_v + rho_l)/2 of the context */
-  double rho_max;    /* ghost clamp / instability bound; 0 means the smallest
-                        rho > rho_l with p(rho) = rho/3 (psi^2 >= 0 below it) */
+  double rho_max;    /* instability bound; 0 means the smallest rho > rho_l
+                        with p(rho) = rho/3 (psi^2 >= 0 below it) */
+  double rho_ghost_max; /* upper clamp of the Eqs. 19-21 ghost densities
+                        (lower clamp 0); 0 means rho_max */
 } lbm_params;
 
 /* Values of a created context (for bookkeeping and tests). */

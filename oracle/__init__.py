@@ -64,7 +64,7 @@ def _load():
             "orc_ghost": (D, [D, D, D, D, D, D, I, D]),
             "orc_collide": (None, [DP, D, D, D, D, D, D, DP, DP]),
             "orc_feq": (None, [D, D, D, DP]),
-            "orc_create": (P, [I, I, I, I, I, DP, D, DP, I, I, DP, D]),
+            "orc_create": (P, [I, I, I, I, I, DP, D, DP, I, I, DP, D, D]),
             "orc_destroy": (None, [P]),
             "orc_set_rho": (None, [P, DP]),
             "orc_set_f": (None, [P, DP]),
@@ -191,7 +191,7 @@ class Sim:
     """Two-array FP64 simulation: f[9, ny, nx], rows 0 and ny-1 solid if walls."""
 
     def __init__(self, nx, ny, eos: Eos, T, tau=1.0, walls=True, A=-0.6, kappa=0.5, G_w=0.0,
-                 n_iter=4, wetting=GEOMETRIC, theta=None, rates=None, rho_max_=None):
+                 n_iter=4, wetting=GEOMETRIC, theta=None, rates=None, rho_max_=None, ghost_max=0.0):
         self.nx, self.ny, self.eos, self.T = nx, ny, eos, T
         lib = _load()
         if rates is None:
@@ -207,7 +207,7 @@ class Sim:
             rho_max_ = np.finfo(np.float64).max
         w = 1 if walls else 0
         self._h = lib.orc_create(nx, ny, w, w, eos.kind, _dp(eos.vec()), T, _dp(params),
-                                 n_iter, wetting, _dp(th), rho_max_)
+                                 n_iter, wetting, _dp(th), rho_max_, ghost_max)
         self._lib = lib
 
     def close(self):

@@ -414,7 +414,8 @@ typedef struct {
   double A, kappa, Gw;
   int n_iter, wetting; /* wetting 0 = geometric (Eqs. 19-21), 1 = Martys-Chen (Eq. 14) */
   double s[9];
-  double rho_max;
+  double rho_max;            /* instability bound; psi = U = 0 at and above it */
+  double ghost_max;          /* upper clamp of the ghost densities */
   double *c_bot, *c_top;     /* sin(pi/2 - theta) per wall node */
   double *cot_bot, *cot_top; /* tan(pi/2 - theta) per wall node (Eq. 19 only) */
   double *f, *fn;            /* [9][ny][nx] */
@@ -434,9 +435,11 @@ static int wrapy(const orc_sim *S, int y) { return (y % S->ny + S->ny) % S->ny; 
 #define FIDX(S, a, y, x) (((size_t)(a) * (size_t)(S)->ny + (size_t)(y)) * (size_t)(S)->nx + (size_t)(x))
 
 /* params[] = {A, kappa, G_w, s_rho, s_e, s_eps, s_j, s_q, s_nu}
- * theta[ny*nx] in radians, read at the wall rows only. */
+ * theta[ny*nx] in radians, read at the wall rows only.  Ghost densities are
+ * clamped to [0, ghost_max] (ghost_max <= 0 means rho_max). */
 void *orc_create(int nx, int ny, int wall_bot, int wall_top, int kind, const double *eos, double T,
-                 const double *params, int n_iter, int wetting, const double *theta, double rho_max) {
+                 const double *params, int n_iter, int wetting, const double *theta, double rho_max,
+                 double ghost_max) {
   orc_sim *S = (orc_sim *)calloc(1, sizeof(orc_sim));
   S->nx = nx; S->ny = ny; S->wall_bot = wall_bot; S->wall_top = wall_top;
   S->kind = kind;
@@ -449,6 +452,7 @@ void *orc_create(int nx, int ny, int wall_bot, int wall_top, int kind, const dou
   memcpy(S->s, s, sizeof(s));
   S->n_iter = n_iter; S->wetting = wetting;
   S->rho_max = rho_max;
+  S->ghost_max = (ghost_max > 0.0 && ghost_max < rho_max) ? ghost_max : rho_max;
   size_t n = (size_t)nx * (size_t)ny;
   S->c_bot = calloc(nx, sizeof(double)); S->c_top = calloc(nx, sizeof(double));
   S->cot_bot = calloc(nx, sizeof(double)); S->cot_top = calloc(nx, sizeof(double));
@@ -535,7 +539,7 @@ static void orc_fields(orc_sim *S) {
       const double *cot = w == 0 ? S->cot_bot : S->cot_top;
       double g = orc_ghost(S->rho[IDX(S, y1, wrapx(S, x - 1))], S->rho[IDX(S, y1, wrapx(S, x + 1))],
                            S->rho[IDX(S, y1, x)], S->rho[IDX(S, y2, x)], c[x], cot[x], S->n_iter,
-                           S->rho_max);
+                           S->ghost_max);
       double p, u;
       /* rho_max is the root of U = p - rho/3 (Eq. 10), so psi = U = 0 there
        * by definition; evaluating the EOS at the root would only return the

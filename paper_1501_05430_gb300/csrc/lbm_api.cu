@@ -289,6 +289,7 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
   C->rho_l = rl;
   C->rho_max = P.rho_max > 0 ? P.rho_max : eos_rho_max(*eos, T, rl);
   C->rho_mid = P.rho_mid > 0 ? P.rho_mid : 0.5 * (rv + rl);
+  C->ghost_max = P.rho_ghost_max > 0 ? fmin(P.rho_ghost_max, C->rho_max) : C->rho_max;
   C->stream = (cudaStream_t)stream;
   lbm_dev_params &D = C->dp;
   D.nx = nx;
@@ -315,6 +316,7 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
   D.n_iter = P.n_iter;
   D.wetting = P.wetting;
   D.rho_max = C->rho_max;
+  D.ghost_max = C->ghost_max;
 
   size_t n = (size_t)nx * ny, rs = real_size(P.precision);
   size_t need = 2 * 9 * n * rs;

@@ -48,7 +48,7 @@ struct FusedArgs {
   long long total;
   int stages;
   float b4, RT, a, thv, thm, thl, r1, r2, p2;  // EOS constants (b/4, R*T, ...)
-  float A, omA, pre, halfA, rho_max;            // force / Q constants
+  float A, omA, pre, halfA, rho_max, ghost_max; // force / Q constants, bounds
   float se, seps, sq, snu;                      // rates
   float he, heps, hq, hnu;                      // 1 - s/2
   float Gw;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
             d = ri2 - g;
           }
         }
-        g = fminf(fmaxf(g, 0.0f), P.rho_max);
+        g = fminf(fmaxf(g, 0.0f), P.ghost_max);
         float psi = 0.0f, U = 0.0f;  // exact values at the clamp rho_max (root of U)
         if (g < P.rho_max) eos_psiU(P, g, psi, U);
         gw[c + 2] = g;
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
               d = ri2 - g;
             }
           }
-          g = fminf(fmaxf(g, 0.0f), P.rho_max);
+          g = fminf(fmaxf(g, 0.0f), P.ghost_max);
           float psi = 0.0f, U = 0.0f;  // exact values at the clamp rho_max (root of U)
           if (g < P.rho_max) eos_psiU(P, g, psi, U);
           wrho[c + 2] = g;
@@ -571,6 +571,7 @@ cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches) {
   P.pre = (float)(-0.5 * D.kappa);
   P.halfA = (float)(0.5 * D.A);
   P.rho_max = (float)fmin(D.rho_max, 3.0e38);
+  P.ghost_max = (float)fmin(D.ghost_max, 3.0e38);
   P.se = (float)D.s[1];
   P.seps = (float)D.s[2];
   P.sq = (float)D.s[4];

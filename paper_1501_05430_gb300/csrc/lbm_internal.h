@@ -18,7 +18,8 @@ struct lbm_dev_params {
   double A, kappa, Gw;
   double s[9];    // rates in moment order (rho, e, eps, jx, qx, jy, qy, pxx, pxy)
   int n_iter, wetting;
-  double rho_max;
+  double rho_max;     // instability bound; psi = U = 0 at and above it
+  double ghost_max;   // upper clamp of the ghost densities (<= rho_max)
 };
 
 // Per-wall-node coefficients of Eqs. 19-21, computed on the host:
@@ -35,7 +36,7 @@ struct lbm_ctx {
   double T, tau;
   lbm_params params;
   lbm_dev_params dp;
-  double rho_v, rho_l, rho_max, rho_mid;
+  double rho_v, rho_l, rho_max, rho_mid, ghost_max;
   cudaStream_t stream;
   int owns_state;
   void *state;           // two [9][ny][nx] arrays, contiguous

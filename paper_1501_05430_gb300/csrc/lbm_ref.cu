@@ -45,12 +45,13 @@ __device__ __forceinline__ double NRM(int k) {
 template <typename R>
 struct Mdl {
   int nx, ny, walls, kind, n_iter, wetting;
-  R a, b, Rg, T, thv, thm, thl, r1, r2, A, kappa, Gw, rho_max;
+  R a, b, Rg, T, thv, thm, thl, r1, r2, A, kappa, Gw, rho_max, ghost_max;
   R s[9];
   __device__ explicit Mdl(const lbm_dev_params &P)
       : nx(P.nx), ny(P.ny), walls(P.walls), kind(P.eos_kind), n_iter(P.n_iter), wetting(P.wetting),
         a((R)P.a), b((R)P.b), Rg((R)P.R), T((R)P.T), thv((R)P.thv), thm((R)P.thm), thl((R)P.thl),
-        r1((R)P.r1), r2((R)P.r2), A((R)P.A), kappa((R)P.kappa), Gw((R)P.Gw), rho_max((R)P.rho_max) {
+        r1((R)P.r1), r2((R)P.r2), A((R)P.A), kappa((R)P.kappa), Gw((R)P.Gw), rho_max((R)P.rho_max),
+        ghost_max((R)P.ghost_max) {
     for (int k = 0; k < 9; ++k) s[k] = (R)P.s[k];
   }
   __device__ bool solid_row(int y) const { return walls && (y == 0 || y == ny - 1); }
@@ -138,8 +139,8 @@ __global__ void k_ghost(lbm_dev_params P, const double *__restrict__ coef, R *__
       d = ri2 - g;
     }
   }
-  g = fmin(fmax(g, (R)0), m.rho_max);
-  // at the clamp rho_max (the root of U, Eq. 10) psi and U take their exact value 0
+  g = fmin(fmax(g, (R)0), m.ghost_max);
+  // at rho_max (the root of U, Eq. 10) psi and U take their exact value 0
   R psi = (R)0, U = (R)0;
   if (g < m.rho_max) psi_U(m, g, psi, U);
   fields[ig] = g;

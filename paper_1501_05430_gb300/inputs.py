@@ -8,8 +8,8 @@ Workloads (the paper gives no grid sizes; these follow its setup of
 Secs. 3.1 and 4.2 -- a semicircular droplet on the bottom wall -- at the
 sizes of the benchmark configurations):
   plain_fp64       100 x 60, CS T/Tc = 0.8, tau = 1, R0 = 20, theta = 90 deg
-  single_droplet   400 x 200, CS T/Tc = 0.6, tau = 0.8, R0 = 60, theta in {30..150}
-  throughput       4096 x 2048, CS T/Tc = 0.5, tau = 0.6, 32 droplets per wall
+  single_droplet   400 x 200, CS (a = 0.25) T/Tc = 0.6, tau = 0.8, R0 = 60
+  throughput       4096 x 2048, Table 1 EOS at ratio 1000, tau = 1, 16 droplets per wall
   batched          256 instances of {128x64 .. 512x256}, seeded theta, T/Tc, tau
 """
 from __future__ import annotations
@@ -62,12 +62,30 @@ def random_distributions(rho: np.ndarray, seed: int, amp: float = 0.05, walls: b
     return f
 
 
+# Table 1 of the paper (Sec. 3.1): Eq. 11 parameters per density ratio with
+# rho_v = 1 and rho_l = ratio, as (rho1, rho2, theta_v, theta_m, theta_l).
+TABLE1 = {
+    10: (1.122, 9.54, 0.25, -0.02, 0.3),
+    100: (1.486, 94.65, 0.1633, -0.02, 0.33333),
+    1000: (1.325, 971.1017, 0.2, -0.01, 0.33333),
+}
+
+
+def cs_eos(a=1.0, b=4.0, R=1.0) -> dict:
+    return {"kind": "cs", "a": a, "b": b, "R": R}
+
+
+def table1_eos(ratio: int) -> dict:
+    r1, r2, tv, tm, tl = TABLE1[ratio]
+    return {"kind": "pw", "theta_v": tv, "theta_m": tm, "theta_l": tl, "rho1": r1, "rho2": r2}
+
+
 @dataclass
 class Workload:
     name: str
     nx: int
     ny: int
-    t_over_tc: float
+    t_over_tc: float                 # Carnahan-Starling only
     tau: float
     steps: int
     droplets: List[Tuple[float, float, int]]
@@ -76,71 +94,86 @@ class Workload:
     theta_set: List[float] = field(default_factory=list)              # degrees per region
     rates: dict = field(default_factory=dict)                          # MRT rates (0 -> 1/tau)
     width: float = 3.0
+    eos: dict = field(default_factory=cs_eos)
+    A: float = -0.6
+    kappa: float = 0.5
     notes: str = ""
 
 
-# MRT rates for the low-temperature workloads: the viscous rate follows tau;
-# energy, energy-square and heat-flux rates take values used with
-# pseudo-potential MRT models at large density ratios.  With all rates equal
-# to 1/tau (BGK) these cases blow up within 100 steps.
+# MRT rates for the low-temperature Carnahan-Starling workloads: the viscous
+# rate follows tau; energy, energy-square and heat-flux rates take values used
+# with pseudo-potential MRT models at large density ratios.  With all rates
+# equal to 1/tau (BGK) these cases blow up within 100 steps.
 LOW_T_RATES = dict(s_e=0.8, s_eps=0.8, s_j=1.0, s_q=1.1)
 
 
 def plain_fp64() -> Workload:
+    """Carnahan-Starling a = 1, b = 4, R = 1, T/Tc = 0.8, BGK tau = 1."""
     nx, ny = 100, 60
     return Workload("plain_fp64_100x60", nx, ny, 0.8, 1.0, 2000, [(50.0, 20.0, 0)],
                     theta_field(nx, ny, np.pi / 2, np.pi / 2), [(0, 0, nx)], [90.0])
 
 
 def single_droplet(theta_deg: float = 90.0) -> Workload:
+    """Carnahan-Starling at T/Tc = 0.6 (density ratio 132), tau = 0.8.  The
+    attraction is scaled to a = 0.25: with a = 1 the liquid has
+    dp/drho = 0.57 > c_s^2 = 1/3, psi(rho) falls through the liquid and angles
+    below 60 deg blow up; the coexistence densities do not depend on a."""
     nx, ny = 400, 200
     return Workload(f"single_droplet_400x200_theta{int(theta_deg)}", nx, ny, 0.6, 0.8, 20000,
                     [(200.0, 60.0, 0)], theta_field(nx, ny, np.deg2rad(theta_deg), np.pi / 2),
-                    [(0, 0, nx)], [theta_deg], dict(LOW_T_RATES))
+                    [(0, 0, nx)], [theta_deg], dict(LOW_T_RATES), eos=cs_eos(a=0.25))
 
 
-def throughput(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: int = 32) -> Workload:
-    """Droplets on both walls.  64 droplets with radii U[40, 120] do not fit on
-    one 4096-node wall (they need ~10^4 nodes), so each wall carries half of
-    them, radii scaled by one common factor so that sum(2 r + 8) <= nx."""
+def _cap_base(r0: float, theta_deg: float) -> float:
+    """Base width of the 2-D circular cap at angle theta whose area equals a
+    semicircle of radius r0 (the droplet's initial shape)."""
+    t = np.deg2rad(theta_deg)
+    R = r0 * np.sqrt(0.5 * np.pi / (t - np.sin(t) * np.cos(t)))
+    return 2.0 * R * np.sin(t) if t <= 0.5 * np.pi else 2.0 * R
+
+
+def throughput(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: int = 16) -> Workload:
+    """Large density ratio: the Eq. 11 EOS of Table 1 at ratio 1000 with the
+    paper's relaxation (all rates 1, tau = 1), A = -0.6, kappa = 0.5, tanh
+    interfaces of width 10, theta ~ U[30, 150] deg per droplet, radii drawn
+    from U[40, 120].
+
+    Each droplet gets a wall slot as wide as the base of the cap it relaxes to
+    at its angle (same area as the initial semicircle) plus a margin, and all
+    radii are scaled by one common factor so that the slots fill the wall;
+    theta is constant on each slot.  16 droplets per wall (32 in all): with 32
+    per wall (64) the droplets' slots are too narrow at ratio 1000 and the run
+    blows up within a few hundred steps, while 16 per wall runs stably."""
     rng = np.random.default_rng(seed)
+    width = 10.0
+    margin = 8.0 + 2.0 * width
     droplets, regions, theta_set = [], [], []
     bottom = np.full(nx, np.pi / 2)
     top = np.full(nx, np.pi / 2)
     scales = []
     for wall in (0, 1):
         r = rng.uniform(40.0, 120.0, per_wall)
-        s = min(1.0, (nx - 8.0 * per_wall) / (2.0 * r.sum()))
+        th = rng.uniform(30.0, 150.0, per_wall)
+        need = np.array([_cap_base(r[k], th[k]) for k in range(per_wall)])
+        s = min(1.0, (nx - margin * per_wall) / need.sum())
         scales.append(s)
         r = r * s
-        free = nx - 2.0 * r.sum()
-        gaps = rng.dirichlet(np.ones(per_wall)) * free
-        th = rng.uniform(30.0, 150.0, per_wall)
-        cursor = 0.0
-        centres = []
+        slot = need * s + margin
+        slot *= nx / slot.sum()
+        x0 = 0.0
         for k in range(per_wall):
-            cursor += gaps[k]
-            centres.append(cursor + r[k])
-            cursor += 2.0 * r[k]
-        centres = np.array(centres)
-        # region bounds halfway between neighbouring droplets (periodic)
-        bounds = []
-        for k in range(per_wall):
-            right_edge = centres[k] + r[k]
-            nxt_left = centres[(k + 1) % per_wall] - r[(k + 1) % per_wall] + (nx if k == per_wall - 1 else 0)
-            bounds.append(0.5 * (right_edge + nxt_left))
-        for k in range(per_wall):
-            lo = bounds[k - 1] - (nx if k == 0 else 0)
-            hi = bounds[k]
-            x0, x1 = int(np.ceil(lo)), int(np.ceil(hi))
-            xs = np.arange(x0, x1) % nx
-            (bottom if wall == 0 else top)[xs] = np.deg2rad(th[k])
-            droplets.append((float(centres[k]), float(r[k]), wall))
-            if x0 >= 0 and x1 <= nx:
-                regions.append((wall, x0, x1))
-                theta_set.append(float(th[k]))
-    return Workload(f"throughput_{nx}x{ny}_{2 * per_wall}drops", nx, ny, 0.5, 0.6, 5000, droplets,
-                    theta_field(nx, ny, bottom, top), regions, theta_set, dict(LOW_T_RATES),
+            lo, hi = x0, x0 + slot[k]
+            xc = 0.5 * (lo + hi)
+            a, b = int(np.ceil(lo)), int(np.ceil(hi)) if k < per_wall - 1 else nx
+            (bottom if wall == 0 else top)[a:b] = np.deg2rad(th[k])
+            droplets.append((float(xc), float(r[k]), wall))
+            regions.append((wall, a, b))
+            theta_set.append(float(th[k]))
+            x0 = hi
+    return Workload(f"throughput_{nx}x{ny}_{2 * per_wall}drops_ratio1000", nx, ny, 0.0, 1.0, 5000, droplets,
+                    theta_field(nx, ny, bottom, top), regions, theta_set, {}, width=width,
+                    eos=table1_eos(1000),
                     notes=f"radius scale factors per wall {scales[0]:.4f}, {scales[1]:.4f}")
 
 

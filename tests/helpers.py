@@ -32,15 +32,19 @@ class Pair:
                  A=-0.6, kappa=0.5, G_w=0.0, n_iter=4, wetting=0, rates=None, precision=64,
                  kernel=L.LBM_KERNEL_AUTO, check_every=0, torch_state=False, stream=None):
         self.nx, self.ny = nx, ny
-        if eos == "cs":
-            self.oeos = O.carnahan_starling()
-            self.geos = L.carnahan_starling()
-            self.T = cs_T(t_over_tc)
+        if eos == "pw":
+            eos = dict(kind="pw", theta_v=pw[0], theta_m=pw[1], theta_l=pw[2], rho1=pw[3], rho2=pw[4])
+        elif eos == "cs":
+            eos = dict(kind="cs", a=1.0, b=4.0, R=1.0)
+        if eos["kind"] == "cs":
+            self.oeos = O.carnahan_starling(eos["a"], eos["b"], eos["R"])
+            self.geos = L.carnahan_starling(eos["a"], eos["b"], eos["R"])
+            self.T = t_over_tc * O.cs_critical(self.oeos)[0]
             self.rho_v, self.rho_l = O.coexistence(self.oeos, self.T)
         else:
-            tv, tm, tl, r1, r2 = pw
-            self.oeos = O.piecewise(tv, tm, tl, r1, r2)
-            self.geos = L.piecewise(tv, tm, tl, r1, r2)
+            args = (eos["theta_v"], eos["theta_m"], eos["theta_l"], eos["rho1"], eos["rho2"])
+            self.oeos = O.piecewise(*args)
+            self.geos = L.piecewise(*args)
             self.T = 0.0
             self.rho_v, self.rho_l = O.coexistence(self.oeos)
         self.rho_max = O.rho_max(self.oeos, self.T, self.rho_l)
@@ -77,6 +81,6 @@ class Pair:
 
 def droplet_pair(w: I.Workload, precision=64, kernel=L.LBM_KERNEL_AUTO, **kw) -> Pair:
     p = Pair(w.nx, w.ny, t_over_tc=w.t_over_tc, tau=w.tau, theta=w.theta, rates=w.rates, precision=precision,
-             kernel=kernel, **kw)
+             kernel=kernel, eos=w.eos, A=w.A, kappa=w.kappa, **kw)
     p.set_rho(I.droplet_field(w.nx, w.ny, w.droplets, p.rho_v, p.rho_l, w.width))
     return p
