@@ -167,13 +167,14 @@ def cpu_oracle_rate(w, budget_nodes_steps: float, steps_cap: int = 3):
     r = dict(s_rho=0.0, s_e=w.rates.get("s_e", inv), s_eps=w.rates.get("s_eps", inv), s_j=w.rates.get("s_j", inv),
              s_q=w.rates.get("s_q", inv), s_nu=inv)
     full = w.nx * (w.ny - 2)
-    if budget_nodes_steps >= full * steps_cap:
-        nx, ny, steps = w.nx, w.ny, steps_cap
+    if budget_nodes_steps >= full:
+        nx, ny = w.nx, w.ny
+        steps = int(max(1, min(steps_cap, budget_nodes_steps // full)))
     else:
         steps = 1
-        frac = max(budget_nodes_steps / full, 1e-4)
-        nx = max(64, int(w.nx * np.sqrt(frac)) // 4 * 4)
-        ny = max(16, int(w.ny * np.sqrt(frac)))
+        frac = budget_nodes_steps / full
+        nx = min(w.nx, max(64, int(w.nx * np.sqrt(frac)) // 4 * 4))
+        ny = min(w.ny, max(16, int(w.ny * np.sqrt(frac))))
     from paper_1501_05430_gb300 import inputs as I
 
     rho = I.droplet_field(w.nx, w.ny, w.droplets, rho_v, rho_l, w.width)

@@ -31,11 +31,13 @@
 
 namespace {
 
-constexpr int W = 128;             // columns per strip = consumer threads
-constexpr int NTHREADS = W + 32;   // + one producer / halo warp
-constexpr int HB = 4;              // halo box width (16 bytes of floats)
-constexpr int WIN = W + 4;         // window columns: c = -2 .. W+1 at index c+2
-constexpr int NSLOT = 4;           // window rows (ring)
+constexpr int NC = 2;                    // columns per consumer thread
+constexpr int NCONS = 128;               // consumer threads (4 warps)
+constexpr int W = NC * NCONS;            // columns per strip
+constexpr int NTHREADS = NCONS + 32;     // + one producer / halo warp
+constexpr int HB = 4;                    // halo box width (16 bytes of floats)
+constexpr int WIN = W + 4;               // window columns: c = -2 .. W+1 at index c+2
+constexpr int NSLOT = 4;                 // window rows (ring)
 constexpr int MAIN_BYTES = 9 * W * 4;
 constexpr int HALO_BYTES = 9 * HB * 4;
 constexpr int HALO_PAD = 256;
@@ -47,7 +49,7 @@ struct FusedArgs {
   int nstrips, nrows, y0;
   long long total;
   int stages;
-  float b4, RT, a, thv, thm, thl, r1, r2, p2;  // EOS constants (b/4, R*T, ...)
+  float b4, RT, a, thv, thm, thl, r1, r2, p2;   // EOS constants (b/4, R*T, ...)
   float A, omA, pre, halfA, rho_max, ghost_max; // force / Q constants, bounds
   float se, seps, sq, snu;                      // rates
   float he, heps, hq, hnu;                      // 1 - s/2
@@ -124,21 +126,132 @@ struct Seq {
   __device__ bool solid(const FusedArgs &P) const { return P.walls && (v == 0 || v == P.ny - 1); }
 };
 
-__device__ __forceinline__ void eos_psiU(const FusedArgs &P, float rho, float &psi, float &U) {
+// sqrt for x >= 0 through the hardware reciprocal square root; exactly 0 at 0.
+__device__ __forceinline__ float sqrt0(float x) { return x * rsqrtf(fmaxf(x, 1.17549435e-38f)); }
+
+// Window entry of one node: rho, psi, U (Eq. 10 with the Carnahan-Starling or
+// Eq. 11 EOS) and psi^2.
+__device__ __forceinline__ float4 eos_node(const FusedArgs &P, float rho) {
   float p;
   if (P.kind == LBM_EOS_CARNAHAN_STARLING) {
     float e = P.b4 * rho;
     float om = 1.0f - e;
     float num = fmaf(e, fmaf(e, 1.0f - e, 1.0f), 1.0f);
-    float den = om * om * om;
-    p = rho * P.RT * num * __frcp_rn(den) - P.a * rho * rho;
+    p = rho * P.RT * __fdividef(num, om * om * om) - P.a * rho * rho;
   } else {
-    if (rho <= P.r1) p = rho * P.thv;
-    else if (rho <= P.r2) p = fmaf(rho - P.r1, P.thm, P.r1 * P.thv);
-    else p = fmaf(rho - P.r2, P.thl, P.p2);
+    p = rho <= P.r1 ? rho * P.thv : (rho <= P.r2 ? fmaf(rho - P.r1, P.thm, P.r1 * P.thv) : fmaf(rho - P.r2, P.thl, P.p2));
   }
-  U = fmaf(rho, -1.0f / 3.0f, p);
-  psi = sqrtf(fmaxf(0.0f, -2.0f * U));
+  float U = fmaf(rho, -1.0f / 3.0f, p);
+  float psi = sqrt0(fmaxf(0.0f, -2.0f * U));
+  return make_float4(rho, psi, U, psi * psi);
+}
+
+// Eqs. 19-21 ghost entry from the boundary row (r1w) and second row (r2w)
+// window rows at column c; coefficient index gx (bottom: c, top: c + nx).
+__device__ __forceinline__ float4 ghost_node(const FusedArgs &P, const float4 *r1w, const float4 *r2w, int c,
+                                             int gx, int top) {
+  float cc = (float)P.coef[top * P.nx + gx], cot = (float)P.coef[(2 + top) * P.nx + gx];
+  float rl = r1w[c + 1].x, rr = r1w[c + 3].x, ri1 = r1w[c + 2].x, ri2 = r2w[c + 2].x;
+  float aa = rr - rl, g;
+  if (P.n_iter <= 0) {
+    g = fmaf(cot, fabsf(aa), ri2);
+  } else {
+    float d = 2.0f * (ri2 - ri1);
+    g = ri2;
+    for (int k = 0; k < P.n_iter; ++k) {
+      g = fmaf(cc, sqrt0(fmaf(aa, aa, d * d)), ri2);
+      d = ri2 - g;
+    }
+  }
+  g = fminf(fmaxf(g, 0.0f), P.ghost_max);
+  // at rho_max (the root of U) psi and U are exactly 0
+  return g < P.rho_max ? eos_node(P, g) : make_float4(g, 0.0f, 0.0f, 0.0f);
+}
+
+// Force (Eq. 9, + Eq. 14), Eq. 17 tensor, MRT collision with the Eq. 6
+// forcing and the Eq. 16 source for one node.  nb[0..8]: window entries at
+// e_0..e_8 (x+e_a, y+e_a); f[9]: its populations; returns f*.
+__device__ __forceinline__ void collide_node(const FusedArgs &P, const float *f, const float4 *nb, int y,
+                                             float *fs) {
+  const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
+  const float rho = nb[0].x, psi0 = nb[0].y, s0 = nb[0].w;
+  const float p1 = nb[1].y, p2 = nb[2].y, p3 = nb[3].y, p4 = nb[4].y;
+  const float p5 = nb[5].y, p6 = nb[6].y, p7 = nb[7].y, p8 = nb[8].y;
+  // Eq. 9: F = -A sum w U e + (1 - A) psi sum w psi e   (G = -1)
+  float spx = fmaf(w1, p1 - p3, w2 * ((p5 - p6) + (p8 - p7)));
+  float spy = fmaf(w1, p2 - p4, w2 * ((p5 + p6) - (p7 + p8)));
+  float sux = fmaf(w1, nb[1].z - nb[3].z, w2 * ((nb[5].z - nb[6].z) + (nb[8].z - nb[7].z)));
+  float suy = fmaf(w1, nb[2].z - nb[4].z, w2 * ((nb[5].z + nb[6].z) - (nb[7].z + nb[8].z)));
+  float cpsi = P.omA * psi0;
+  float Fx = fmaf(cpsi, spx, -P.A * sux);
+  float Fy = fmaf(cpsi, spy, -P.A * suy);
+  if (P.wetting == LBM_WET_MARTYS_CHEN && P.walls) {
+    // Eq. 14 for flat solid rows: sum_a w_a S e_a = (0, -1/2) below, (0, 1/2) above
+    float ssy = (y == 1 ? -0.5f : 0.0f) + (y == P.ny - 2 ? 0.5f : 0.0f);
+    Fy = fmaf(-P.Gw * psi0, ssy, Fy);
+  }
+  // Eq. 17 with its G/2 prefactor
+  float sd = (p5 + p6) + (p7 + p8);
+  float qxx1 = fmaf(w1, (p1 + p3) - 2.0f * psi0, w2 * fmaf(-4.0f, psi0, sd));
+  float qyy1 = fmaf(w1, (p2 + p4) - 2.0f * psi0, w2 * fmaf(-4.0f, psi0, sd));
+  float qxy1 = w2 * ((p5 + p7) - (p6 + p8));
+  float td = (nb[5].w + nb[6].w) + (nb[7].w + nb[8].w);
+  float qxx2 = fmaf(w1, (nb[1].w + nb[3].w) - 2.0f * s0, w2 * fmaf(-4.0f, s0, td));
+  float qyy2 = fmaf(w1, (nb[2].w + nb[4].w) - 2.0f * s0, w2 * fmaf(-4.0f, s0, td));
+  float qxy2 = w2 * ((nb[5].w + nb[7].w) - (nb[6].w + nb[8].w));
+  float c1 = P.omA * psi0;
+  float Qxx = P.pre * fmaf(c1, qxx1, P.halfA * qxx2);
+  float Qyy = P.pre * fmaf(c1, qyy1, P.halfA * qyy2);
+  float Qxy = P.pre * fmaf(c1, qxy1, P.halfA * qxy2);
+  // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy)
+  float a13 = f[1] + f[3], s13 = f[1] - f[3];
+  float a24 = f[2] + f[4], s24 = f[2] - f[4];
+  float d57 = f[5] - f[7], d86 = f[8] - f[6];
+  float ax = a13 + a24, dg = (f[5] + f[6]) + (f[7] + f[8]);
+  float jx = s13 + (d57 + d86);
+  float jy = s24 + (d57 - d86);
+  float me = fmaf(-4.0f, f[0], fmaf(2.0f, dg, -ax));
+  float meps = fmaf(4.0f, f[0], fmaf(-2.0f, ax, dg));
+  float mqx = fmaf(-2.0f, s13, d57 + d86);
+  float mqy = fmaf(-2.0f, s24, d57 - d86);
+  float mpxx = a13 - a24;
+  float mpxy = (f[5] + f[7]) - (f[6] + f[8]);
+  // velocity with the half-force shift
+  float ir = __fdividef(1.0f, rho);
+  float vx = fmaf(0.5f, Fx, jx) * ir, vy = fmaf(0.5f, Fy, jy) * ir;
+  float rvx = rho * vx, rvy = rho * vy;
+  float v2 = fmaf(vx, vx, vy * vy);
+  float vF = fmaf(vx, Fx, vy * Fy);
+  // relaxation (Eq. 15) with forcing S (Eq. 6) and source C (Eq. 16)
+  float es = fmaf(-P.se, fmaf(-rho, fmaf(3.0f, v2, -2.0f), me), me) + fmaf(P.he * 6.0f, vF, 1.5f * P.se * (Qxx + Qyy));
+  float epss = fmaf(-P.seps, fmaf(-rho, fmaf(-3.0f, v2, 1.0f), meps), meps) - P.heps * 6.0f * vF;
+  float qxs = fmaf(-P.sq, mqx + rvx, mqx) - P.hq * Fx;
+  float qys = fmaf(-P.sq, mqy + rvy, mqy) - P.hq * Fy;
+  float pxxs = fmaf(-P.snu, fmaf(-rvx, vx, fmaf(rvy, vy, mpxx)), mpxx) +
+               fmaf(P.hnu * 2.0f, fmaf(vx, Fx, -vy * Fy), -P.snu * (Qxx - Qyy));
+  float pxys = fmaf(-P.snu, fmaf(-rvx, vy, mpxy), mpxy) + fmaf(P.hnu, fmaf(vx, Fy, vy * Fx), -P.snu * Qxy);
+  float jxs = jx + Fx, jys = jy + Fy;
+  // back to populations: f* = M^T diag(1/N) m*.  rho/9 is rounded through one
+  // correction step: a plain product with a rounded 1/9 biases the mass.
+  const float c9 = 1.0f / 9.0f;
+  float r0 = rho * c9;
+  r0 = fmaf(fmaf(-9.0f, r0, rho), c9, r0);
+  float r1 = es * (1.0f / 36.0f), r2 = epss * (1.0f / 36.0f);
+  float r3 = jxs * (1.0f / 6.0f), r4 = qxs * (1.0f / 12.0f), r5 = jys * (1.0f / 6.0f), r6 = qys * (1.0f / 12.0f);
+  float r7 = pxxs * 0.25f, r8 = pxys * 0.25f;
+  fs[0] = fmaf(4.0f, r2 - r1, r0);
+  float Aax = fmaf(-2.0f, r2, r0 - r1);
+  float Bdg = fmaf(2.0f, r1, r0 + r2);
+  float X1 = fmaf(-2.0f, r4, r3), Y1 = fmaf(-2.0f, r6, r5);
+  fs[1] = (Aax + X1) + r7;
+  fs[3] = (Aax - X1) + r7;
+  fs[2] = (Aax + Y1) - r7;
+  fs[4] = (Aax - Y1) - r7;
+  float X2 = r3 + r4, Y2 = r5 + r6;
+  fs[5] = (Bdg + X2) + (Y2 + r8);
+  fs[6] = (Bdg - X2) + (Y2 - r8);
+  fs[7] = (Bdg - X2) - (Y2 - r8);
+  fs[8] = (Bdg + X2) - (Y2 + r8);
 }
 
 __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUtensorMap tm_main,
@@ -148,18 +261,19 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int S = P.stages;
   unsigned char *stage_base = smem;
-  unsigned long long *bars = (unsigned long long *)(smem + (size_t)S * STAGE_BYTES);
-  float *win = (float *)(bars + S);  // [NSLOT][3][WIN]: rho, psi, U
-  volatile int &s_abort = *(volatile int *)(win + NSLOT * 3 * WIN);
+  float4 *win = (float4 *)(smem + (size_t)S * STAGE_BYTES);  // [NSLOT][WIN]: rho, psi, U, psi^2
+  unsigned long long *bars = (unsigned long long *)(win + NSLOT * WIN);
+  volatile int &s_abort = *(volatile int *)(bars + S);
 
   const int tid = threadIdx.x;
-  const bool consumer = tid < W;
+  const bool consumer = tid < NCONS;
   const int lane = tid & 31;
-  const bool producer = tid == W;  // lane 0 of the last warp
+  const bool producer = tid == NCONS;  // lane 0 of the last warp
   const long long G = gridDim.x;
   const long long u0 = (long long)blockIdx.x * P.total / G;
   const long long u1 = (long long)(blockIdx.x + 1) * P.total / G;
   const size_t n = (size_t)P.nx * P.ny;
+  const bool geo = P.wetting == LBM_WET_GEOMETRIC;
 
   if (tid == 0) {
     s_abort = 0;
@@ -170,10 +284,15 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
   }
   __syncthreads();
 
-  // ---- producer state -----------------------------------------------------
+  // ---- producer -------------------------------------------------------------
   Seq ps{};
   long long issued = 0;
   auto issue_until = [&](long long limit) {
+    if (ps.has && issued < limit) {
+      // order the generic-proxy reads of the stages being refilled before
+      // the asynchronous-proxy writes of the new loads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     while (ps.has && issued < limit) {
       if (!ps.solid(P)) {
         int s = (int)(issued % S);
@@ -202,263 +321,173 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
     issue_until(S);
   }
 
-  // ---- consumer / halo state ------------------------------------------------
+  // ---- row sweep --------------------------------------------------------------
+  // A stage is read twice: when its row enters the window (iteration i) and
+  // when that row is collided (iteration i+1, after the barrier).  It is free
+  // after the barrier of iteration i+2, so the producer refills up to
+  // (loads consumed by the end of iteration i-2) + S.
   Seq cs;
   cs.init(P, u0, u1);
-  long long consumed = 0;
+  long long consumed = 0, cons_m1 = 0, cons_m2 = 0;
+  int prev_stage = 0;
   long long it = 0;
-  float fcur[9], fnext[9];
-#pragma unroll
-  for (int a = 0; a < 9; ++a) fcur[a] = fnext[a] = 0.0f;
   bool bad = false;
-  const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
+  const int cA = NC * tid;  // first of this consumer's columns
 
   while (cs.has) {
     const int v = cs.v;
     const int x0 = cs.strip * W;
     const int wr = min(W, P.nx - x0);
-    const int slot = (int)(it & 3);
-    float *wrho = win + (size_t)slot * 3 * WIN;
-    const bool geo = P.wetting == LBM_WET_GEOMETRIC;
-    // column handled by this thread in the row phase
-    int c = consumer ? tid : (lane == 0 ? -1 : lane == 1 ? wr : lane == 2 ? -2 : lane == 3 ? wr + 1 : -100);
-    bool need2 = P.walls && geo && ((v == 1 && cs.ya == 1) || (v == P.ny - 2 && cs.yb == P.ny - 1));
-    bool active = consumer ? (c < wr) : (lane < 2 || (lane < 4 && need2));
+    float4 *wcur = win + (size_t)(it & 3) * WIN;
+    const bool need2 = P.walls && geo && ((v == 1 && cs.ya == 1) || (v == P.ny - 2 && cs.yb == P.ny - 1));
+    // halo lanes: 0 -> c = -1, 1 -> c = wr, 2 -> c = -2, 3 -> c = wr + 1
+    const int hc = lane == 0 ? -1 : lane == 1 ? wr : lane == 2 ? -2 : wr + 1;
+    const bool hact = !consumer && (lane < 2 || (lane < 4 && need2));
+    const bool cact = consumer && cA < wr;
+    int cur_stage = prev_stage;
     if (!cs.solid(P)) {
-      int s = (int)(consumed % S);
-      unsigned parity = (unsigned)((consumed / S) & 1);
-      unsigned bar = smem_u32(&bars[s]);
-      if (!mbar_wait(bar, parity)) {
+      const int s = (int)(consumed % S);
+      cur_stage = s;
+      if (!mbar_wait(smem_u32(&bars[s]), (unsigned)((consumed / S) & 1))) {
         s_abort = 1;
         atomicOr(P.flag + 1, 1);
       }
       const float *st = (const float *)(stage_base + (size_t)s * STAGE_BYTES);
-      if (active) {
-        const float *src;
-        int stride;
-        if (c >= 0 && c < wr) { src = st + c; stride = W; }
-        else if (c < 0) { src = st + MAIN_BYTES / 4 + (HB + c); stride = HB; }
-        else { src = st + (MAIN_BYTES + HALO_PAD) / 4 + (c - wr); stride = HB; }
-        float f[9];
+      if (cact) {
+        float ra = 0.0f, rb = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 9; ++a) f[a] = src[a * stride];
-        float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        float psi, U;
-        eos_psiU(P, rho, psi, U);
-        wrho[c + 2] = rho;
-        wrho[WIN + c + 2] = psi;
-        wrho[2 * WIN + c + 2] = U;
-        if (!(rho > 0.0f) || rho > P.rho_max) bad = true;
-        if (consumer) {
-#pragma unroll
-          for (int a = 0; a < 9; ++a) fnext[a] = f[a];
+        for (int a = 0; a < 9; ++a) {
+          float2 fv = *(const float2 *)(st + a * W + cA);
+          ra += fv.x;
+          rb += fv.y;
         }
+        float4 ea = eos_node(P, ra), eb = eos_node(P, rb);
+        wcur[cA + 2] = ea;
+        wcur[cA + 3] = eb;
+        bad |= !(ra > 0.0f) || ra > P.rho_max || !(rb > 0.0f) || rb > P.rho_max;
+      } else if (hact) {
+        const float *src = hc < 0 ? st + MAIN_BYTES / 4 + (HB + hc) : st + (MAIN_BYTES + HALO_PAD) / 4 + (hc - wr);
+        float r = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) r += src[a * HB];
+        wcur[hc + 2] = eos_node(P, r);
       }
       ++consumed;
       // bottom ghost row (Eqs. 19-21): rows 1 and 2 are now in the window
-      if (P.walls && geo && cs.ya == 1 && v == 2 && (consumer ? c < wr : lane < 2)) {
-        const float *r1w = win + (size_t)((it - 1) & 3) * 3 * WIN;  // row 1
-        float *gw = win + (size_t)((it - 2) & 3) * 3 * WIN;         // row 0
-        int gx = x0 + c;
-        gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-        float cc = (float)P.coef[gx], cot = (float)P.coef[2 * P.nx + gx];
-        float rl = r1w[c + 1], rr = r1w[c + 3], ri1 = r1w[c + 2], ri2 = wrho[c + 2];
-        float aa = rr - rl, g;
-        if (P.n_iter <= 0) {
-          g = fmaf(cot, fabsf(aa), ri2);
-        } else {
-          float d = 2.0f * (ri2 - ri1);
-          g = ri2;
-          for (int k = 0; k < P.n_iter; ++k) {
-            g = fmaf(cc, sqrtf(fmaf(aa, aa, d * d)), ri2);
-            d = ri2 - g;
-          }
+      if (P.walls && geo && cs.ya == 1 && v == 2) {
+        const float4 *r1w = win + (size_t)((it - 1) & 3) * WIN;  // row 1
+        float4 *gw = win + (size_t)((it - 2) & 3) * WIN;         // row 0
+        if (cact) {
+#pragma unroll
+          for (int j = 0; j < NC; ++j) gw[cA + j + 2] = ghost_node(P, r1w, wcur, cA + j, x0 + cA + j, 0);
+        } else if (!consumer && lane < 2) {
+          int gx = x0 + hc;
+          gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+          gw[hc + 2] = ghost_node(P, r1w, wcur, hc, gx, 0);
         }
-        g = fminf(fmaxf(g, 0.0f), P.ghost_max);
-        float psi = 0.0f, U = 0.0f;  // exact values at the clamp rho_max (root of U)
-        if (g < P.rho_max) eos_psiU(P, g, psi, U);
-        gw[c + 2] = g;
-        gw[WIN + c + 2] = psi;
-        gw[2 * WIN + c + 2] = U;
-      }
-    } else if (v == 0) {
-      // bottom solid row: Martys-Chen carries zero potential there; the
-      // geometric ghost values are written once rows 1 and 2 are known
-      if (!geo && (consumer ? c < wr : lane < 2)) {
-        wrho[c + 2] = 0.0f;
-        wrho[WIN + c + 2] = 0.0f;
-        wrho[2 * WIN + c + 2] = 0.0f;
       }
     } else {
-      // top solid row: ghost from rows ny-2 (previous slot) and ny-3
-      if (consumer ? c < wr : lane < 2) {
-        if (geo) {
-          const float *r1w = win + (size_t)((it - 1) & 3) * 3 * WIN;  // row ny-2
-          const float *r2w = win + (size_t)((it - 2) & 3) * 3 * WIN;  // row ny-3
-          int gx = x0 + c;
+      // solid row: zero potential (Martys-Chen), or the top ghost row from rows
+      // ny-2 and ny-3 (the bottom ghost row is filled at v == 2)
+      const bool top = v != 0;
+      const float4 *r1w = win + (size_t)((it - 1) & 3) * WIN;
+      const float4 *r2w = win + (size_t)((it - 2) & 3) * WIN;
+      if (cact) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          if (!geo) wcur[cA + j + 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          else if (top) wcur[cA + j + 2] = ghost_node(P, r1w, r2w, cA + j, x0 + cA + j, 1);
+        }
+      } else if (!consumer && lane < 2) {
+        if (!geo) {
+          wcur[hc + 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else if (top) {
+          int gx = x0 + hc;
           gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-          float cc = (float)P.coef[P.nx + gx], cot = (float)P.coef[3 * P.nx + gx];
-          float rl = r1w[c + 1], rr = r1w[c + 3], ri1 = r1w[c + 2], ri2 = r2w[c + 2];
-          float aa = rr - rl, g;
-          if (P.n_iter <= 0) {
-            g = fmaf(cot, fabsf(aa), ri2);
-          } else {
-            float d = 2.0f * (ri2 - ri1);
-            g = ri2;
-            for (int k = 0; k < P.n_iter; ++k) {
-              g = fmaf(cc, sqrtf(fmaf(aa, aa, d * d)), ri2);
-              d = ri2 - g;
-            }
-          }
-          g = fminf(fmaxf(g, 0.0f), P.ghost_max);
-          float psi = 0.0f, U = 0.0f;  // exact values at the clamp rho_max (root of U)
-          if (g < P.rho_max) eos_psiU(P, g, psi, U);
-          wrho[c + 2] = g;
-          wrho[WIN + c + 2] = psi;
-          wrho[2 * WIN + c + 2] = U;
-        } else {
-          wrho[c + 2] = 0.0f;
-          wrho[WIN + c + 2] = 0.0f;
-          wrho[2 * WIN + c + 2] = 0.0f;
+          wcur[hc + 2] = ghost_node(P, r1w, r2w, hc, gx, 1);
         }
       }
     }
     __syncthreads();
     if (s_abort) break;
 
-    // ---- collide row v-1 --------------------------------------------------
-    if (consumer && c < wr && v >= cs.ya + 1 && v <= cs.yb) {
+    // ---- collide row v-1 (its populations are still in stage prev_stage) ----
+    if (cact && v >= cs.ya + 1 && v <= cs.yb) {
       const int y = v - 1;
-      const float *wm = win + (size_t)((it - 2) & 3) * 3 * WIN;  // row y-1
-      const float *w0 = win + (size_t)((it - 1) & 3) * 3 * WIN;  // row y
-      const float *wp = wrho;                                      // row y+1
-      const int i0 = c + 2;
-      float psi0 = w0[WIN + i0];
-      float rho = w0[i0];
-      // neighbour potentials, e1..e8
-      float p1 = w0[WIN + i0 + 1], p3 = w0[WIN + i0 - 1];
-      float p2 = wp[WIN + i0], p4 = wm[WIN + i0];
-      float p5 = wp[WIN + i0 + 1], p6 = wp[WIN + i0 - 1];
-      float p7 = wm[WIN + i0 - 1], p8 = wm[WIN + i0 + 1];
-      float u1 = w0[2 * WIN + i0 + 1], u3 = w0[2 * WIN + i0 - 1];
-      float u2 = wp[2 * WIN + i0], u4 = wm[2 * WIN + i0];
-      float u5 = wp[2 * WIN + i0 + 1], u6 = wp[2 * WIN + i0 - 1];
-      float u7 = wm[2 * WIN + i0 - 1], u8 = wm[2 * WIN + i0 + 1];
-      // Eq. 9
-      float spx = fmaf(w1, p1 - p3, w2 * ((p5 - p6) + (p8 - p7)));
-      float spy = fmaf(w1, p2 - p4, w2 * ((p5 + p6) - (p7 + p8)));
-      float sux = fmaf(w1, u1 - u3, w2 * ((u5 - u6) + (u8 - u7)));
-      float suy = fmaf(w1, u2 - u4, w2 * ((u5 + u6) - (u7 + u8)));
-      // F = -A sum w U e - (1-A) G psi sum w psi e with G = -1
-      float cpsi = P.omA * psi0;  // (1 - A) psi
-      float Fx = fmaf(cpsi, spx, -P.A * sux);
-      float Fy = fmaf(cpsi, spy, -P.A * suy);
-      if (P.wetting == LBM_WET_MARTYS_CHEN && P.walls) {
-        // Eq. 14 for flat solid rows: sum_a w_a S e_a = (0, -1/2) below, (0, 1/2) above
-        float ssy = (y == 1 ? -0.5f : 0.0f) + (y == P.ny - 2 ? 0.5f : 0.0f);
-        Fy = fmaf(-P.Gw * psi0, ssy, Fy);
+      const float4 *wm = win + (size_t)((it - 2) & 3) * WIN;  // row y-1
+      const float4 *w0 = win + (size_t)((it - 1) & 3) * WIN;  // row y
+      const float4 *wp = wcur;                                 // row y+1
+      const float *st = (const float *)(stage_base + (size_t)prev_stage * STAGE_BYTES);
+      float f2[9][NC];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        float2 fv = *(const float2 *)(st + a * W + cA);
+        f2[a][0] = fv.x;
+        f2[a][1] = fv.y;
       }
-      // Eq. 17 (with its G/2 prefactor)
-      float sd = (p5 + p6) + (p7 + p8);
-      float q0 = 4.0f * psi0;
-      float qxx1 = fmaf(w1, (p1 + p3) - 0.5f * q0, w2 * (sd - q0));
-      float qyy1 = fmaf(w1, (p2 + p4) - 0.5f * q0, w2 * (sd - q0));
-      float qxy1 = w2 * ((p5 + p7) - (p6 + p8));
-      float s0 = psi0 * psi0;
-      float t1 = p1 * p1, t2 = p2 * p2, t3 = p3 * p3, t4 = p4 * p4;
-      float t5 = p5 * p5, t6 = p6 * p6, t7 = p7 * p7, t8 = p8 * p8;
-      float td = (t5 + t6) + (t7 + t8);
-      float qxx2 = fmaf(w1, (t1 + t3) - 2.0f * s0, w2 * (td - 4.0f * s0));
-      float qyy2 = fmaf(w1, (t2 + t4) - 2.0f * s0, w2 * (td - 4.0f * s0));
-      float qxy2 = w2 * ((t5 + t7) - (t6 + t8));
-      float c1 = P.omA * psi0;
-      float Qxx = P.pre * fmaf(c1, qxx1, P.halfA * qxx2);
-      float Qyy = P.pre * fmaf(c1, qyy1, P.halfA * qyy2);
-      float Qxy = P.pre * fmaf(c1, qxy1, P.halfA * qxy2);
-      // moments of f (Eq. 4 ordering)
-      const float *f = fcur;
-      float a13 = f[1] + f[3], s13 = f[1] - f[3];
-      float a24 = f[2] + f[4], s24 = f[2] - f[4];
-      float d57 = f[5] - f[7], d86 = f[8] - f[6];
-      float ax = a13 + a24, dg = (f[5] + f[6]) + (f[7] + f[8]);
-      float jx = s13 + d57 + d86;
-      float jy = s24 + d57 - d86;
-      float me = fmaf(-4.0f, f[0], fmaf(2.0f, dg, -ax));
-      float meps = fmaf(4.0f, f[0], fmaf(-2.0f, ax, dg));
-      float mqx = fmaf(-2.0f, s13, d57 + d86);
-      float mqy = fmaf(-2.0f, s24, d57 - d86);
-      float mpxx = a13 - a24;
-      float mpxy = (f[5] + f[7]) - (f[6] + f[8]);
-      // velocity with the half-force shift
-      float ir = __frcp_rn(rho);
-      float vx = fmaf(0.5f, Fx, jx) * ir, vy = fmaf(0.5f, Fy, jy) * ir;
-      float v2 = fmaf(vx, vx, vy * vy);
-      float vF = fmaf(vx, Fx, vy * Fy);
-      // relaxation (Eq. 15) with forcing S (Eq. 6) and source C (Eq. 16)
-      float e_eq = rho * fmaf(3.0f, v2, -2.0f);
-      float eps_eq = rho * fmaf(-3.0f, v2, 1.0f);
-      float es = fmaf(-P.se, me - e_eq, me) + P.he * 6.0f * vF + 1.5f * P.se * (Qxx + Qyy);
-      float epss = fmaf(-P.seps, meps - eps_eq, meps) - P.heps * 6.0f * vF;
-      float qxs = fmaf(-P.sq, mqx + rho * vx, mqx) - P.hq * Fx;
-      float qys = fmaf(-P.sq, mqy + rho * vy, mqy) - P.hq * Fy;
-      float pxxs = fmaf(-P.snu, mpxx - rho * (vx * vx - vy * vy), mpxx) +
-                   P.hnu * 2.0f * (vx * Fx - vy * Fy) - P.snu * (Qxx - Qyy);
-      float pxys = fmaf(-P.snu, mpxy - rho * vx * vy, mpxy) + P.hnu * fmaf(vx, Fy, vy * Fx) - P.snu * Qxy;
-      float jxs = jx + Fx, jys = jy + Fy;
-      // back to populations: f* = M^T diag(1/N) m*
-      // rho/9 correctly rounded: a biased 1/9 constant would leak mass every step
-      float r0 = __fdiv_rn(rho, 9.0f), r1 = es * (1.0f / 36.0f), r2 = epss * (1.0f / 36.0f);
-      float r3 = jxs * (1.0f / 6.0f), r4 = qxs * (1.0f / 12.0f), r5 = jys * (1.0f / 6.0f),
-            r6 = qys * (1.0f / 12.0f);
-      float r7 = pxxs * 0.25f, r8 = pxys * 0.25f;
-      float fs[9];
-      fs[0] = fmaf(4.0f, r2 - r1, r0);
-      float Aax = fmaf(-2.0f, r2, r0 - r1);
-      float Bdg = fmaf(2.0f, r1, r0 + r2);
-      float X1 = fmaf(-2.0f, r4, r3), Y1 = fmaf(-2.0f, r6, r5);
-      fs[1] = (Aax + X1) + r7;
-      fs[3] = (Aax - X1) + r7;
-      fs[2] = (Aax + Y1) - r7;
-      fs[4] = (Aax - Y1) - r7;
-      float X2 = r3 + r4, Y2 = r5 + r6;
-      fs[5] = (Bdg + X2) + (Y2 + r8);
-      fs[6] = (Bdg - X2) + (Y2 - r8);
-      fs[7] = (Bdg - X2) - (Y2 - r8);
-      fs[8] = (Bdg + X2) - (Y2 + r8);
-      // streaming with half-way bounce-back
-      const int x = x0 + c;
-      const int xm = x == 0 ? P.nx - 1 : x - 1, xp = x == P.nx - 1 ? 0 : x + 1;
+      float fs2[9][NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int i0 = cA + j + 2;
+        float4 nb[9];
+        nb[0] = w0[i0];
+        nb[1] = w0[i0 + 1];
+        nb[2] = wp[i0];
+        nb[3] = w0[i0 - 1];
+        nb[4] = wm[i0];
+        nb[5] = wp[i0 + 1];
+        nb[6] = wp[i0 - 1];
+        nb[7] = wm[i0 - 1];
+        nb[8] = wm[i0 + 1];
+        float f[9], fs[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) f[a] = f2[a][j];
+        collide_node(P, f, nb, y, fs);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) fs2[a][j] = fs[a];
+      }
+      // streaming with half-way bounce-back; columns x, x+1 of this thread
+      const int x = x0 + cA;
+      const int xm = x == 0 ? P.nx - 1 : x - 1;          // left of the first column
+      const int xp = x + 2 == P.nx ? 0 : x + 2;          // right of the second column
       const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
       const bool wall_dn = P.walls && y == 1, wall_up = P.walls && y == P.ny - 2;
       float *out = P.fout;
       const size_t ry = (size_t)y * P.nx, rym = (size_t)ym * P.nx, ryp = (size_t)yp * P.nx;
-      out[0 * n + ry + x] = fs[0];
-      out[1 * n + ry + xp] = fs[1];
-      out[3 * n + ry + xm] = fs[3];
+      *(float2 *)(out + ry + x) = make_float2(fs2[0][0], fs2[0][1]);
+      // e1 = (1, 0): x -> x + 1
+      out[1 * n + ry + x + 1] = fs2[1][0];
+      out[1 * n + ry + xp] = fs2[1][1];
+      // e3 = (-1, 0)
+      out[3 * n + ry + xm] = fs2[3][0];
+      out[3 * n + ry + x] = fs2[3][1];
       if (wall_up) {
-        out[4 * n + ry + x] = fs[2];
-        out[7 * n + ry + x] = fs[5];
-        out[8 * n + ry + x] = fs[6];
+        *(float2 *)(out + 4 * n + ry + x) = make_float2(fs2[2][0], fs2[2][1]);
+        *(float2 *)(out + 7 * n + ry + x) = make_float2(fs2[5][0], fs2[5][1]);
+        *(float2 *)(out + 8 * n + ry + x) = make_float2(fs2[6][0], fs2[6][1]);
       } else {
-        out[2 * n + ryp + x] = fs[2];
-        out[5 * n + ryp + xp] = fs[5];
-        out[6 * n + ryp + xm] = fs[6];
+        *(float2 *)(out + 2 * n + ryp + x) = make_float2(fs2[2][0], fs2[2][1]);
+        out[5 * n + ryp + x + 1] = fs2[5][0];
+        out[5 * n + ryp + xp] = fs2[5][1];
+        out[6 * n + ryp + xm] = fs2[6][0];
+        out[6 * n + ryp + x] = fs2[6][1];
       }
       if (wall_dn) {
-        out[2 * n + ry + x] = fs[4];
-        out[5 * n + ry + x] = fs[7];
-        out[6 * n + ry + x] = fs[8];
+        *(float2 *)(out + 2 * n + ry + x) = make_float2(fs2[4][0], fs2[4][1]);
+        *(float2 *)(out + 5 * n + ry + x) = make_float2(fs2[7][0], fs2[7][1]);
+        *(float2 *)(out + 6 * n + ry + x) = make_float2(fs2[8][0], fs2[8][1]);
       } else {
-        out[4 * n + rym + x] = fs[4];
-        out[7 * n + rym + xm] = fs[7];
-        out[8 * n + rym + xp] = fs[8];
+        *(float2 *)(out + 4 * n + rym + x) = make_float2(fs2[4][0], fs2[4][1]);
+        out[7 * n + rym + xm] = fs2[7][0];
+        out[7 * n + rym + x] = fs2[7][1];
+        out[8 * n + rym + x + 1] = fs2[8][0];
+        out[8 * n + rym + xp] = fs2[8][1];
       }
     }
-    if (consumer) {
-#pragma unroll
-      for (int a = 0; a < 9; ++a) fcur[a] = fnext[a];
-    }
-    if (producer) issue_until(consumed + S);
+    prev_stage = cur_stage;
+    if (producer) issue_until(cons_m2 + S);
+    cons_m2 = cons_m1;
+    cons_m1 = consumed;
     ++it;
     cs.next(P);
   }
@@ -504,7 +533,7 @@ bool encode(CUtensorMap *m, void *base, int nx, int ny, int boxw) {
 }
 
 size_t smem_bytes(int stages) {
-  return 128 + (size_t)stages * STAGE_BYTES + (size_t)stages * 8 + (size_t)NSLOT * 3 * WIN * sizeof(float) + 16;
+  return 128 + (size_t)stages * STAGE_BYTES + (size_t)NSLOT * WIN * sizeof(float4) + (size_t)stages * 8 + 16;
 }
 
 }  // namespace
@@ -517,7 +546,7 @@ int lbm_fused_plan(lbm_ctx *C) {
     if (!encode((CUtensorMap *)C->tmaps[2 * b], C->f[b], C->nx, C->ny, W)) return 0;
     if (!encode((CUtensorMap *)C->tmaps[2 * b + 1], C->f[b], C->nx, C->ny, HB)) return 0;
   }
-  int stages = 6;
+  int stages = 5;
   size_t smem = smem_bytes(stages);
   if (cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
