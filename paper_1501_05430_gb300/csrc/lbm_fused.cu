@@ -26,6 +26,7 @@
 //    mostly from L2.  psi and U never go to HBM.
 #include <cuda.h>
 #include <math.h>
+#include <stdlib.h>
 
 #include "lbm_internal.h"
 
@@ -49,7 +50,8 @@ struct FusedArgs {
   int nstrips, nrows, y0;
   long long total;
   int stages;
-  float b4, RT, a, thv, thm, thl, r1, r2, p2;   // EOS constants (b/4, R*T, ...)
+  float b4, RT, a, r1, r2, pc0, pc1, pc2;      // EOS constants (b/4, R*T, a; Eq. 11 break-
+                                                // points and slopes folded into -2U)
   float A, omA, pre, halfA, rho_max, ghost_max; // force / Q constants, bounds
   float se, seps, sq, snu;                      // rates
   float he, heps, hq, hnu;                      // 1 - s/2
@@ -69,14 +71,17 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
+// Test an mbarrier phase; a thread that finds it incomplete is suspended by
+// the hardware for up to ~0.5 ms (the suspend-time hint) or until the phase
+// completes, instead of spinning through issue slots.
 __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
   unsigned ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(500000u)
       : "memory");
   return ok != 0;
 }
@@ -87,7 +92,7 @@ __device__ bool mbar_wait(unsigned bar, unsigned parity) {
   unsigned long long t0 = gtimer();
   for (unsigned it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
-    if ((it & 63) == 0 && gtimer() - t0 > kWaitNs) return false;
+    if (gtimer() - t0 > kWaitNs) return false;
   }
 }
 
@@ -129,21 +134,23 @@ struct Seq {
 // sqrt for x >= 0 through the hardware reciprocal square root; exactly 0 at 0.
 __device__ __forceinline__ float sqrt0(float x) { return x * rsqrtf(fmaxf(x, 1.17549435e-38f)); }
 
-// Window entry of one node: rho, psi, U (Eq. 10 with the Carnahan-Starling or
-// Eq. 11 EOS) and psi^2.
+// Window entry of one node: rho, psi and psi^2 = -2U (Eq. 10 with G = -1 and
+// the Carnahan-Starling or Eq. 11 EOS; psi = 0 where U >= 0).  U itself is
+// recovered as -psi^2/2 wherever the force needs it.
 __device__ __forceinline__ float4 eos_node(const FusedArgs &P, float rho) {
-  float p;
+  float m2u;  // -2U = 2 (rho/3 - p)
   if (P.kind == LBM_EOS_CARNAHAN_STARLING) {
     float e = P.b4 * rho;
     float om = 1.0f - e;
     float num = fmaf(e, fmaf(e, 1.0f - e, 1.0f), 1.0f);
-    p = rho * P.RT * __fdividef(num, om * om * om) - P.a * rho * rho;
+    float p = rho * P.RT * __fdividef(num, om * om * om) - P.a * rho * rho;
+    m2u = fmaf(rho, 2.0f / 3.0f, -2.0f * p);
   } else {
-    p = rho <= P.r1 ? rho * P.thv : (rho <= P.r2 ? fmaf(rho - P.r1, P.thm, P.r1 * P.thv) : fmaf(rho - P.r2, P.thl, P.p2));
+    // Eq. 11 written branch-free: p = rho th_v + (th_m - th_v)(rho - rho1)^+ + (th_l - th_m)(rho - rho2)^+
+    m2u = fmaf(P.pc2, fmaxf(rho - P.r2, 0.0f), fmaf(P.pc1, fmaxf(rho - P.r1, 0.0f), P.pc0 * rho));
   }
-  float U = fmaf(rho, -1.0f / 3.0f, p);
-  float psi = sqrt0(fmaxf(0.0f, -2.0f * U));
-  return make_float4(rho, psi, U, psi * psi);
+  float psi2 = fmaxf(0.0f, m2u);
+  return make_float4(rho, sqrt0(psi2), psi2, 0.0f);
 }
 
 // Eqs. 19-21 ghost entry from the boundary row (r1w) and second row (r2w)
@@ -165,72 +172,81 @@ __device__ __forceinline__ float4 ghost_node(const FusedArgs &P, const float4 *r
   }
   g = fminf(fmaxf(g, 0.0f), P.ghost_max);
   // at rho_max (the root of U) psi and U are exactly 0
-  return g < P.rho_max ? eos_node(P, g) : make_float4(g, 0.0f, 0.0f, 0.0f);
+  return g < P.rho_max ? eos_node(P, g) : make_float4(g, 0.0f, 0.0f, 0.0f);  // psi = U = 0 at rho_max
 }
 
 // Force (Eq. 9, + Eq. 14), Eq. 17 tensor, MRT collision with the Eq. 6
 // forcing and the Eq. 16 source for one node.  nb[0..8]: window entries at
-// e_0..e_8 (x+e_a, y+e_a); f[9]: its populations; returns f*.
+// e_0..e_8 (x+e_a, y+e_a); f[9]: its populations; returns f*.  UNIT: every
+// non-conserved rate equals 1 (the relaxation matrix diag(0,1,...,1) of
+// Sec. 3.1), so m* = m_eq + S/2 + C needs only rho and j from f.
+template <bool UNIT>
 __device__ __forceinline__ void collide_node(const FusedArgs &P, const float *f, const float4 *nb, int y,
                                              float *fs) {
   const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
-  const float rho = nb[0].x, psi0 = nb[0].y, s0 = nb[0].w;
-  const float p1 = nb[1].y, p2 = nb[2].y, p3 = nb[3].y, p4 = nb[4].y;
-  const float p5 = nb[5].y, p6 = nb[6].y, p7 = nb[7].y, p8 = nb[8].y;
-  // Eq. 9: F = -A sum w U e + (1 - A) psi sum w psi e   (G = -1)
-  float spx = fmaf(w1, p1 - p3, w2 * ((p5 - p6) + (p8 - p7)));
-  float spy = fmaf(w1, p2 - p4, w2 * ((p5 + p6) - (p7 + p8)));
-  float sux = fmaf(w1, nb[1].z - nb[3].z, w2 * ((nb[5].z - nb[6].z) + (nb[8].z - nb[7].z)));
-  float suy = fmaf(w1, nb[2].z - nb[4].z, w2 * ((nb[5].z + nb[6].z) - (nb[7].z + nb[8].z)));
-  float cpsi = P.omA * psi0;
-  float Fx = fmaf(cpsi, spx, -P.A * sux);
-  float Fy = fmaf(cpsi, spy, -P.A * suy);
+  const float rho = nb[0].x, p0 = nb[0].y;
+  // Eq. 9 (G = -1, U = -psi^2/2) and Eq. 17 (with its G/2 prefactor) weigh
+  // the neighbours' psi and psi^2 with the same two coefficients, so both act
+  // on one combined value per neighbour:
+  //   g_a = (1 - A) psi_0 psi_a + (A/2) psi_a^2
+  //   F   = sum_a w_a g_a e_a,    Q = (-kappa/2) sum_a w_a (g_a - g_0) e_a e_a
+  const float c1 = P.omA * p0;
+  float g[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) g[k] = fmaf(c1, nb[k].y, P.halfA * nb[k].z);
+  const float gd57 = g[5] - g[7], gd86 = g[8] - g[6];
+  float Fx = fmaf(w1, g[1] - g[3], w2 * (gd57 + gd86));
+  float Fy = fmaf(w1, g[2] - g[4], w2 * (gd57 - gd86));
   if (P.wetting == LBM_WET_MARTYS_CHEN && P.walls) {
     // Eq. 14 for flat solid rows: sum_a w_a S e_a = (0, -1/2) below, (0, 1/2) above
     float ssy = (y == 1 ? -0.5f : 0.0f) + (y == P.ny - 2 ? 0.5f : 0.0f);
-    Fy = fmaf(-P.Gw * psi0, ssy, Fy);
+    Fy = fmaf(-P.Gw * p0, ssy, Fy);
   }
-  // Eq. 17 with its G/2 prefactor
-  float sd = (p5 + p6) + (p7 + p8);
-  float qxx1 = fmaf(w1, (p1 + p3) - 2.0f * psi0, w2 * fmaf(-4.0f, psi0, sd));
-  float qyy1 = fmaf(w1, (p2 + p4) - 2.0f * psi0, w2 * fmaf(-4.0f, psi0, sd));
-  float qxy1 = w2 * ((p5 + p7) - (p6 + p8));
-  float td = (nb[5].w + nb[6].w) + (nb[7].w + nb[8].w);
-  float qxx2 = fmaf(w1, (nb[1].w + nb[3].w) - 2.0f * s0, w2 * fmaf(-4.0f, s0, td));
-  float qyy2 = fmaf(w1, (nb[2].w + nb[4].w) - 2.0f * s0, w2 * fmaf(-4.0f, s0, td));
-  float qxy2 = w2 * ((nb[5].w + nb[7].w) - (nb[6].w + nb[8].w));
-  float c1 = P.omA * psi0;
-  float Qxx = P.pre * fmaf(c1, qxx1, P.halfA * qxx2);
-  float Qyy = P.pre * fmaf(c1, qyy1, P.halfA * qyy2);
-  float Qxy = P.pre * fmaf(c1, qxy1, P.halfA * qxy2);
+  const float gs57 = g[5] + g[7], gs68 = g[6] + g[8];
+  const float gq = w2 * fmaf(-4.0f, g[0], gs57 + gs68);
+  const float Qxx = P.pre * fmaf(w1, fmaf(-2.0f, g[0], g[1] + g[3]), gq);
+  const float Qyy = P.pre * fmaf(w1, fmaf(-2.0f, g[0], g[2] + g[4]), gq);
+  const float Qxy = P.pre * (w2 * (gs57 - gs68));
   // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy)
-  float a13 = f[1] + f[3], s13 = f[1] - f[3];
-  float a24 = f[2] + f[4], s24 = f[2] - f[4];
-  float d57 = f[5] - f[7], d86 = f[8] - f[6];
-  float ax = a13 + a24, dg = (f[5] + f[6]) + (f[7] + f[8]);
-  float jx = s13 + (d57 + d86);
-  float jy = s24 + (d57 - d86);
-  float me = fmaf(-4.0f, f[0], fmaf(2.0f, dg, -ax));
-  float meps = fmaf(4.0f, f[0], fmaf(-2.0f, ax, dg));
-  float mqx = fmaf(-2.0f, s13, d57 + d86);
-  float mqy = fmaf(-2.0f, s24, d57 - d86);
-  float mpxx = a13 - a24;
-  float mpxy = (f[5] + f[7]) - (f[6] + f[8]);
+  const float s13 = f[1] - f[3], s24 = f[2] - f[4];
+  const float d57 = f[5] - f[7], d86 = f[8] - f[6];
+  const float jx = s13 + (d57 + d86);
+  const float jy = s24 + (d57 - d86);
   // velocity with the half-force shift
-  float ir = __fdividef(1.0f, rho);
-  float vx = fmaf(0.5f, Fx, jx) * ir, vy = fmaf(0.5f, Fy, jy) * ir;
-  float rvx = rho * vx, rvy = rho * vy;
-  float v2 = fmaf(vx, vx, vy * vy);
-  float vF = fmaf(vx, Fx, vy * Fy);
-  // relaxation (Eq. 15) with forcing S (Eq. 6) and source C (Eq. 16)
-  float es = fmaf(-P.se, fmaf(-rho, fmaf(3.0f, v2, -2.0f), me), me) + fmaf(P.he * 6.0f, vF, 1.5f * P.se * (Qxx + Qyy));
-  float epss = fmaf(-P.seps, fmaf(-rho, fmaf(-3.0f, v2, 1.0f), meps), meps) - P.heps * 6.0f * vF;
-  float qxs = fmaf(-P.sq, mqx + rvx, mqx) - P.hq * Fx;
-  float qys = fmaf(-P.sq, mqy + rvy, mqy) - P.hq * Fy;
-  float pxxs = fmaf(-P.snu, fmaf(-rvx, vx, fmaf(rvy, vy, mpxx)), mpxx) +
-               fmaf(P.hnu * 2.0f, fmaf(vx, Fx, -vy * Fy), -P.snu * (Qxx - Qyy));
-  float pxys = fmaf(-P.snu, fmaf(-rvx, vy, mpxy), mpxy) + fmaf(P.hnu, fmaf(vx, Fy, vy * Fx), -P.snu * Qxy);
-  float jxs = jx + Fx, jys = jy + Fy;
+  const float ir = __fdividef(1.0f, rho);
+  const float vx = fmaf(0.5f, Fx, jx) * ir, vy = fmaf(0.5f, Fy, jy) * ir;
+  const float rvx = rho * vx, rvy = rho * vy;
+  const float v2 = fmaf(vx, vx, vy * vy);
+  const float vF = fmaf(vx, Fx, vy * Fy);
+  const float sQ = Qxx + Qyy, dQ = Qxx - Qyy;
+  float es, epss, qxs, qys, pxxs, pxys;
+  if (UNIT) {
+    // m* = m_eq + S/2 + C with s = 1
+    es = fmaf(rho, fmaf(3.0f, v2, -2.0f), fmaf(3.0f, vF, 1.5f * sQ));
+    epss = fmaf(rho, fmaf(-3.0f, v2, 1.0f), -3.0f * vF);
+    qxs = fmaf(-0.5f, Fx, -rvx);
+    qys = fmaf(-0.5f, Fy, -rvy);
+    pxxs = fmaf(rvx, vx, fmaf(-rvy, vy, fmaf(vx, Fx, fmaf(-vy, Fy, -dQ))));
+    pxys = fmaf(rvx, vy, fmaf(0.5f, fmaf(vx, Fy, vy * Fx), -Qxy));
+  } else {
+    const float a13 = f[1] + f[3], a24 = f[2] + f[4];
+    const float ax = a13 + a24, dg = (f[5] + f[6]) + (f[7] + f[8]);
+    const float me = fmaf(-4.0f, f[0], fmaf(2.0f, dg, -ax));
+    const float meps = fmaf(4.0f, f[0], fmaf(-2.0f, ax, dg));
+    const float mqx = fmaf(-2.0f, s13, d57 + d86);
+    const float mqy = fmaf(-2.0f, s24, d57 - d86);
+    const float mpxx = a13 - a24;
+    const float mpxy = (f[5] + f[7]) - (f[6] + f[8]);
+    // relaxation (Eq. 15) with forcing S (Eq. 6) and source C (Eq. 16)
+    es = fmaf(-P.se, fmaf(-rho, fmaf(3.0f, v2, -2.0f), me), me) + fmaf(P.he * 6.0f, vF, 1.5f * P.se * sQ);
+    epss = fmaf(-P.seps, fmaf(-rho, fmaf(-3.0f, v2, 1.0f), meps), meps) - P.heps * 6.0f * vF;
+    qxs = fmaf(-P.sq, mqx + rvx, mqx) - P.hq * Fx;
+    qys = fmaf(-P.sq, mqy + rvy, mqy) - P.hq * Fy;
+    pxxs = fmaf(-P.snu, fmaf(-rvx, vx, fmaf(rvy, vy, mpxx)), mpxx) +
+           fmaf(P.hnu * 2.0f, fmaf(vx, Fx, -vy * Fy), -P.snu * dQ);
+    pxys = fmaf(-P.snu, fmaf(-rvx, vy, mpxy), mpxy) + fmaf(P.hnu, fmaf(vx, Fy, vy * Fx), -P.snu * Qxy);
+  }
+  const float jxs = jx + Fx, jys = jy + Fy;
   // back to populations: f* = M^T diag(1/N) m*.  rho/9 is rounded through one
   // correction step: a plain product with a rounded 1/9 biases the mass.
   const float c9 = 1.0f / 9.0f;
@@ -254,14 +270,15 @@ __device__ __forceinline__ void collide_node(const FusedArgs &P, const float *f,
   fs[8] = (Bdg + X2) - (Y2 + r8);
 }
 
-__global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUtensorMap tm_main,
-                                                    const __grid_constant__ CUtensorMap tm_halo, FusedArgs P) {
+template <bool UNIT>
+__global__ void __launch_bounds__(NTHREADS, 4) k_fused(const __grid_constant__ CUtensorMap tm_main,
+                                                       const __grid_constant__ CUtensorMap tm_halo, FusedArgs P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA destinations must be 128-byte aligned in shared memory
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int S = P.stages;
   unsigned char *stage_base = smem;
-  float4 *win = (float4 *)(smem + (size_t)S * STAGE_BYTES);  // [NSLOT][WIN]: rho, psi, U, psi^2
+  float4 *win = (float4 *)(smem + (size_t)S * STAGE_BYTES);  // [NSLOT][WIN]: rho, psi, psi^2, -
   unsigned long long *bars = (unsigned long long *)(win + NSLOT * WIN);
   volatile int &s_abort = *(volatile int *)(bars + S);
 
@@ -286,8 +303,8 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
 
   // ---- producer -------------------------------------------------------------
   Seq ps{};
-  long long issued = 0;
-  auto issue_until = [&](long long limit) {
+  int issued = 0, put_stage = 0;  // loads issued; ring slot of the next load
+  auto issue_until = [&](int limit) {
     if (ps.has && issued < limit) {
       // order the generic-proxy reads of the stages being refilled before
       // the asynchronous-proxy writes of the new loads
@@ -295,7 +312,8 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
     }
     while (ps.has && issued < limit) {
       if (!ps.solid(P)) {
-        int s = (int)(issued % S);
+        const int s = put_stage;
+        put_stage = put_stage + 1 == S ? 0 : put_stage + 1;
         unsigned bar = smem_u32(&bars[s]);
         unsigned char *st = stage_base + (size_t)s * STAGE_BYTES;
         int x0 = ps.strip * W;
@@ -328,11 +346,14 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
   // (loads consumed by the end of iteration i-2) + S.
   Seq cs;
   cs.init(P, u0, u1);
-  long long consumed = 0, cons_m1 = 0, cons_m2 = 0;
+  int consumed = 0, cons_m1 = 0, cons_m2 = 0;  // loads consumed (after iterations i, i-1, i-2)
+  int get_stage = 0;                            // ring slot of the next load to consume
+  unsigned get_phase = 0;                       // its mbarrier phase parity
   int prev_stage = 0;
-  long long it = 0;
+  int it = 0;
   bool bad = false;
-  const int cA = NC * tid;  // first of this consumer's columns
+  // consumer t owns columns t and t + NCONS: unit-stride shared-memory and
+  // global accesses across the warp for each of the two
 
   while (cs.has) {
     const int v = cs.v;
@@ -343,28 +364,35 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
     // halo lanes: 0 -> c = -1, 1 -> c = wr, 2 -> c = -2, 3 -> c = wr + 1
     const int hc = lane == 0 ? -1 : lane == 1 ? wr : lane == 2 ? -2 : wr + 1;
     const bool hact = !consumer && (lane < 2 || (lane < 4 && need2));
-    const bool cact = consumer && cA < wr;
+    const bool cact0 = consumer && tid < wr;
+    const bool cact1 = consumer && tid + NCONS < wr;
+    const bool cact = cact0;
     int cur_stage = prev_stage;
     if (!cs.solid(P)) {
-      const int s = (int)(consumed % S);
+      const int s = get_stage;
       cur_stage = s;
-      if (!mbar_wait(smem_u32(&bars[s]), (unsigned)((consumed / S) & 1))) {
+      const unsigned ph = get_phase;
+      if (++get_stage == S) {
+        get_stage = 0;
+        get_phase ^= 1u;
+      }
+      if (!mbar_wait(smem_u32(&bars[s]), ph)) {
         s_abort = 1;
         atomicOr(P.flag + 1, 1);
       }
       const float *st = (const float *)(stage_base + (size_t)s * STAGE_BYTES);
       if (cact) {
-        float ra = 0.0f, rb = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-          float2 fv = *(const float2 *)(st + a * W + cA);
-          ra += fv.x;
-          rb += fv.y;
+        for (int j = 0; j < NC; ++j) {
+          const int c = tid + j * NCONS;
+          if (j == 0 || cact1) {
+            const float *q = st + c;
+            float r = (((q[0] + q[W]) + (q[2 * W] + q[3 * W])) + ((q[4 * W] + q[5 * W]) + (q[6 * W] + q[7 * W]))) +
+                      q[8 * W];
+            wcur[c + 2] = eos_node(P, r);
+            bad |= !(r > 0.0f) || r > P.rho_max;
+          }
         }
-        float4 ea = eos_node(P, ra), eb = eos_node(P, rb);
-        wcur[cA + 2] = ea;
-        wcur[cA + 3] = eb;
-        bad |= !(ra > 0.0f) || ra > P.rho_max || !(rb > 0.0f) || rb > P.rho_max;
       } else if (hact) {
         const float *src = hc < 0 ? st + MAIN_BYTES / 4 + (HB + hc) : st + (MAIN_BYTES + HALO_PAD) / 4 + (hc - wr);
         float r = 0.0f;
@@ -379,7 +407,10 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
         float4 *gw = win + (size_t)((it - 2) & 3) * WIN;         // row 0
         if (cact) {
 #pragma unroll
-          for (int j = 0; j < NC; ++j) gw[cA + j + 2] = ghost_node(P, r1w, wcur, cA + j, x0 + cA + j, 0);
+          for (int j = 0; j < NC; ++j) {
+            const int c = tid + j * NCONS;
+            if (j == 0 || cact1) gw[c + 2] = ghost_node(P, r1w, wcur, c, x0 + c, 0);
+          }
         } else if (!consumer && lane < 2) {
           int gx = x0 + hc;
           gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
@@ -395,8 +426,11 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
       if (cact) {
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
-          if (!geo) wcur[cA + j + 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          else if (top) wcur[cA + j + 2] = ghost_node(P, r1w, r2w, cA + j, x0 + cA + j, 1);
+          const int c = tid + j * NCONS;
+          if (j == 0 || cact1) {
+            if (!geo) wcur[c + 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            else if (top) wcur[c + 2] = ghost_node(P, r1w, r2w, c, x0 + c, 1);
+          }
         }
       } else if (!consumer && lane < 2) {
         if (!geo) {
@@ -418,17 +452,19 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
       const float4 *w0 = win + (size_t)((it - 1) & 3) * WIN;  // row y
       const float4 *wp = wcur;                                 // row y+1
       const float *st = (const float *)(stage_base + (size_t)prev_stage * STAGE_BYTES);
-      float f2[9][NC];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        float2 fv = *(const float2 *)(st + a * W + cA);
-        f2[a][0] = fv.x;
-        f2[a][1] = fv.y;
-      }
-      float fs2[9][NC];
+      const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
+      const bool wall_dn = P.walls && y == 1, wall_up = P.walls && y == P.ny - 2;
+      // per-plane output pointers are warp-uniform; each store adds one 32-bit
+      // element offset (9 nx ny < 2^31 is checked at creation)
+      float *const o0p = P.fout, *const o1p = o0p + n, *const o2p = o1p + n, *const o3p = o2p + n;
+      float *const o4p = o3p + n, *const o5p = o4p + n, *const o6p = o5p + n, *const o7p = o6p + n;
+      float *const o8p = o7p + n;
+      const unsigned ry = (unsigned)y * P.nx, rym = (unsigned)ym * P.nx, ryp = (unsigned)yp * P.nx;
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
-        const int i0 = cA + j + 2;
+        const int c = tid + j * NCONS;
+        if (j == 1 && !cact1) break;
+        const int i0 = c + 2;
         float4 nb[9];
         nb[0] = w0[i0];
         nb[1] = w0[i0 + 1];
@@ -441,47 +477,32 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
         nb[8] = wm[i0 + 1];
         float f[9], fs[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) f[a] = f2[a][j];
-        collide_node(P, f, nb, y, fs);
-#pragma unroll
-        for (int a = 0; a < 9; ++a) fs2[a][j] = fs[a];
-      }
-      // streaming with half-way bounce-back; columns x, x+1 of this thread
-      const int x = x0 + cA;
-      const int xm = x == 0 ? P.nx - 1 : x - 1;          // left of the first column
-      const int xp = x + 2 == P.nx ? 0 : x + 2;          // right of the second column
-      const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
-      const bool wall_dn = P.walls && y == 1, wall_up = P.walls && y == P.ny - 2;
-      float *out = P.fout;
-      const size_t ry = (size_t)y * P.nx, rym = (size_t)ym * P.nx, ryp = (size_t)yp * P.nx;
-      *(float2 *)(out + ry + x) = make_float2(fs2[0][0], fs2[0][1]);
-      // e1 = (1, 0): x -> x + 1
-      out[1 * n + ry + x + 1] = fs2[1][0];
-      out[1 * n + ry + xp] = fs2[1][1];
-      // e3 = (-1, 0)
-      out[3 * n + ry + xm] = fs2[3][0];
-      out[3 * n + ry + x] = fs2[3][1];
-      if (wall_up) {
-        *(float2 *)(out + 4 * n + ry + x) = make_float2(fs2[2][0], fs2[2][1]);
-        *(float2 *)(out + 7 * n + ry + x) = make_float2(fs2[5][0], fs2[5][1]);
-        *(float2 *)(out + 8 * n + ry + x) = make_float2(fs2[6][0], fs2[6][1]);
-      } else {
-        *(float2 *)(out + 2 * n + ryp + x) = make_float2(fs2[2][0], fs2[2][1]);
-        out[5 * n + ryp + x + 1] = fs2[5][0];
-        out[5 * n + ryp + xp] = fs2[5][1];
-        out[6 * n + ryp + xm] = fs2[6][0];
-        out[6 * n + ryp + x] = fs2[6][1];
-      }
-      if (wall_dn) {
-        *(float2 *)(out + 2 * n + ry + x) = make_float2(fs2[4][0], fs2[4][1]);
-        *(float2 *)(out + 5 * n + ry + x) = make_float2(fs2[7][0], fs2[7][1]);
-        *(float2 *)(out + 6 * n + ry + x) = make_float2(fs2[8][0], fs2[8][1]);
-      } else {
-        *(float2 *)(out + 4 * n + rym + x) = make_float2(fs2[4][0], fs2[4][1]);
-        out[7 * n + rym + xm] = fs2[7][0];
-        out[7 * n + rym + x] = fs2[7][1];
-        out[8 * n + rym + x + 1] = fs2[8][0];
-        out[8 * n + rym + xp] = fs2[8][1];
+        for (int a = 0; a < 9; ++a) f[a] = st[a * W + c];
+        collide_node<UNIT>(P, f, nb, y, fs);
+        // streaming with half-way bounce-back
+        const int x = x0 + c;
+        const unsigned xm = x == 0 ? P.nx - 1 : x - 1, xp = x == P.nx - 1 ? 0 : x + 1;
+        o0p[ry + x] = fs[0];
+        o1p[ry + xp] = fs[1];
+        o3p[ry + xm] = fs[3];
+        if (wall_up) {
+          o4p[ry + x] = fs[2];
+          o7p[ry + x] = fs[5];
+          o8p[ry + x] = fs[6];
+        } else {
+          o2p[ryp + x] = fs[2];
+          o5p[ryp + xp] = fs[5];
+          o6p[ryp + xm] = fs[6];
+        }
+        if (wall_dn) {
+          o2p[ry + x] = fs[4];
+          o5p[ry + x] = fs[7];
+          o6p[ry + x] = fs[8];
+        } else {
+          o4p[rym + x] = fs[4];
+          o7p[rym + xm] = fs[7];
+          o8p[rym + xp] = fs[8];
+        }
       }
     }
     prev_stage = cur_stage;
@@ -494,10 +515,7 @@ __global__ void __launch_bounds__(NTHREADS) k_fused(const __grid_constant__ CUte
 
   if (s_abort && producer) {
     // drain the loads still in flight (bounded) before the CTA exits
-    for (long long k = consumed - 1; k < issued; ++k) {
-      int s = (int)(k % S);
-      mbar_wait(smem_u32(&bars[s]), (unsigned)((k / S) & 1));
-    }
+    for (int k = consumed - 1; k < issued; ++k) mbar_wait(smem_u32(&bars[k % S]), (unsigned)((k / S) & 1));
   }
   if (bad) atomicOr(P.flag, 1);
 }
@@ -546,22 +564,33 @@ int lbm_fused_plan(lbm_ctx *C) {
     if (!encode((CUtensorMap *)C->tmaps[2 * b], C->f[b], C->nx, C->ny, W)) return 0;
     if (!encode((CUtensorMap *)C->tmaps[2 * b + 1], C->f[b], C->nx, C->ny, HB)) return 0;
   }
-  int stages = 5;
+  // tuning knobs (defaults measured on GB300): TMA ring depth and CTAs per SM
+  int stages = 4;
+  if (const char *e = getenv("LBM_FUSED_STAGES")) stages = atoi(e);
+  if (stages < 3 || stages > 12) stages = 4;
   size_t smem = smem_bytes(stages);
-  if (cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  // the diag(0,1,...,1) relaxation of Sec. 3.1 takes the specialised collision
+  const lbm_dev_params &D = C->dp;
+  C->fused_unit = D.s[1] == 1.0 && D.s[2] == 1.0 && D.s[4] == 1.0 && D.s[7] == 1.0;
+  const void *kern = C->fused_unit ? (const void *)k_fused<true> : (const void *)k_fused<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused, NTHREADS, smem) != cudaSuccess || occ < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTHREADS, smem) != cudaSuccess || occ < 1) {
     cudaGetLastError();
     return 0;
   }
   int nstrips = (C->nx + W - 1) / W;
   int nrows = C->walls ? C->ny - 2 : C->ny;
   long long total = (long long)nstrips * nrows;
+  if (const char *e = getenv("LBM_FUSED_CTAS_PER_SM")) {
+    int want = atoi(e);
+    if (want >= 1 && want < occ) occ = want;
+  }
   long long blocks = (long long)nsm * occ;
   if (blocks > total) blocks = total;
   C->tile_w = W;
@@ -589,12 +618,11 @@ cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches) {
   P.b4 = (float)(0.25 * D.b);
   P.RT = (float)(D.R * D.T);
   P.a = (float)D.a;
-  P.thv = (float)D.thv;
-  P.thm = (float)D.thm;
-  P.thl = (float)D.thl;
   P.r1 = (float)D.r1;
   P.r2 = (float)D.r2;
-  P.p2 = (float)(D.r1 * D.thv + (D.r2 - D.r1) * D.thm);
+  P.pc0 = (float)(-2.0 * (D.thv - 1.0 / 3.0));
+  P.pc1 = (float)(-2.0 * (D.thm - D.thv));
+  P.pc2 = (float)(-2.0 * (D.thl - D.thm));
   P.A = (float)D.A;
   P.omA = (float)(1.0 - D.A);
   P.pre = (float)(-0.5 * D.kappa);
@@ -615,7 +643,10 @@ cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches) {
   P.flag = C->d_flag;
   const CUtensorMap *tm = (const CUtensorMap *)C->tmaps[2 * src];
   const CUtensorMap *th = (const CUtensorMap *)C->tmaps[2 * src + 1];
-  k_fused<<<C->tile_blocks, NTHREADS, C->fused_smem, C->stream>>>(*tm, *th, P);
+  if (C->fused_unit)
+    k_fused<true><<<C->tile_blocks, NTHREADS, C->fused_smem, C->stream>>>(*tm, *th, P);
+  else
+    k_fused<false><<<C->tile_blocks, NTHREADS, C->fused_smem, C->stream>>>(*tm, *th, P);
   ++*launches;
   return cudaGetLastError();
 }

@@ -55,7 +55,7 @@ struct lbm_ctx {
   double *d_res;         // small results
   int red_len;
   // fused kernel plan
-  int fused_ok;
+  int fused_ok, fused_unit;  // fused kernel usable; unit-rate specialisation
   int tile_w, tile_blocks, tile_stages, fused_smem;
   unsigned char tmaps[4][128];   // CUtensorMap for f[0], f[1]: main box, halo box
 };
