@@ -32,17 +32,21 @@
 
 namespace {
 
-constexpr int NC = 2;                    // columns per consumer thread
-constexpr int NCONS = 128;               // consumer threads (4 warps)
-constexpr int W = NC * NCONS;            // columns per strip
-constexpr int NTHREADS = NCONS + 32;     // + one producer / halo warp
+constexpr int NCONS = 128;               // threads per CTA (4 warps)
 constexpr int HB = 4;                    // halo box width (16 bytes of floats)
-constexpr int WIN = W + 4;               // window columns: c = -2 .. W+1 at index c+2
 constexpr int NSLOT = 4;                 // window rows (ring)
-constexpr int MAIN_BYTES = 9 * W * 4;
 constexpr int HALO_BYTES = 9 * HB * 4;
 constexpr int HALO_PAD = 256;
-constexpr int STAGE_BYTES = MAIN_BYTES + 2 * HALO_PAD;
+
+// Launch shape for NC columns per thread: strips of W = 128 NC columns.
+template <int NC>
+struct Cfg {
+  static constexpr int W = NC * NCONS;                          // columns per strip
+  static constexpr int WIN = W + 4;                             // window columns c = -2 .. W+1
+  static constexpr int MAIN_BYTES = 9 * W * 4;                  // 9 planes x W floats
+  static constexpr int STAGE_BYTES = MAIN_BYTES + 2 * HALO_PAD;
+  static constexpr int MIN_CTAS = NC == 1 ? 8 : 5;             // register budget per thread
+};
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per bounded wait
 
 struct FusedArgs {
@@ -153,12 +157,12 @@ __device__ __forceinline__ float4 eos_node(const FusedArgs &P, float rho) {
   return make_float4(rho, sqrt0(psi2), psi2, 0.0f);
 }
 
-// Eqs. 19-21 ghost entry from the boundary row (r1w) and second row (r2w)
-// window rows at column c; coefficient index gx (bottom: c, top: c + nx).
-__device__ __forceinline__ float4 ghost_node(const FusedArgs &P, const float4 *r1w, const float4 *r2w, int c,
-                                             int gx, int top) {
+// Eqs. 19-21 ghost entry from the boundary-row (r1) and second-row (r2)
+// densities of the window at column c; coefficient index gx; top: 0 or 1.
+__device__ __forceinline__ float4 ghost_node(const FusedArgs &P, const float *r1, const float *r2, int c, int gx,
+                                             int top) {
   float cc = (float)P.coef[top * P.nx + gx], cot = (float)P.coef[(2 + top) * P.nx + gx];
-  float rl = r1w[c + 1].x, rr = r1w[c + 3].x, ri1 = r1w[c + 2].x, ri2 = r2w[c + 2].x;
+  float rl = r1[c + 1], rr = r1[c + 3], ri1 = r1[c + 2], ri2 = r2[c + 2];
   float aa = rr - rl, g;
   if (P.n_iter <= 0) {
     g = fmaf(cot, fabsf(aa), ri2);
@@ -171,20 +175,19 @@ __device__ __forceinline__ float4 ghost_node(const FusedArgs &P, const float4 *r
     }
   }
   g = fminf(fmaxf(g, 0.0f), P.ghost_max);
-  // at rho_max (the root of U) psi and U are exactly 0
   return g < P.rho_max ? eos_node(P, g) : make_float4(g, 0.0f, 0.0f, 0.0f);  // psi = U = 0 at rho_max
 }
 
 // Force (Eq. 9, + Eq. 14), Eq. 17 tensor, MRT collision with the Eq. 6
-// forcing and the Eq. 16 source for one node.  nb[0..8]: window entries at
-// e_0..e_8 (x+e_a, y+e_a); f[9]: its populations; returns f*.  UNIT: every
+// forcing and the Eq. 16 source for one node.  nb[0..8]: (psi, psi^2) at
+// x+e_0..x+e_8; rho: its density; f[9]: its populations; returns f*.  UNIT: every
 // non-conserved rate equals 1 (the relaxation matrix diag(0,1,...,1) of
 // Sec. 3.1), so m* = m_eq + S/2 + C needs only rho and j from f.
 template <bool UNIT>
-__device__ __forceinline__ void collide_node(const FusedArgs &P, const float *f, const float4 *nb, int y,
+__device__ __forceinline__ void collide_node(const FusedArgs &P, const float *f, const float2 *nb, float rho, int y,
                                              float *fs) {
   const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
-  const float rho = nb[0].x, p0 = nb[0].y;
+  const float p0 = nb[0].x;
   // Eq. 9 (G = -1, U = -psi^2/2) and Eq. 17 (with its G/2 prefactor) weigh
   // the neighbours' psi and psi^2 with the same two coefficients, so both act
   // on one combined value per neighbour:
@@ -193,7 +196,7 @@ __device__ __forceinline__ void collide_node(const FusedArgs &P, const float *f,
   const float c1 = P.omA * p0;
   float g[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) g[k] = fmaf(c1, nb[k].y, P.halfA * nb[k].z);
+  for (int k = 0; k < 9; ++k) g[k] = fmaf(c1, nb[k].x, P.halfA * nb[k].y);
   const float gd57 = g[5] - g[7], gd86 = g[8] - g[6];
   float Fx = fmaf(w1, g[1] - g[3], w2 * (gd57 + gd86));
   float Fy = fmaf(w1, g[2] - g[4], w2 * (gd57 - gd86));
@@ -270,22 +273,26 @@ __device__ __forceinline__ void collide_node(const FusedArgs &P, const float *f,
   fs[8] = (Bdg + X2) - (Y2 + r8);
 }
 
-template <bool UNIT>
-__global__ void __launch_bounds__(NTHREADS, 4) k_fused(const __grid_constant__ CUtensorMap tm_main,
-                                                       const __grid_constant__ CUtensorMap tm_halo, FusedArgs P) {
+template <bool UNIT, int NC>
+__global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
+    k_fused(const __grid_constant__ CUtensorMap tm_main, const __grid_constant__ CUtensorMap tm_halo, FusedArgs P) {
+  constexpr int W = Cfg<NC>::W, WIN = Cfg<NC>::WIN, MAIN_BYTES = Cfg<NC>::MAIN_BYTES;
+  constexpr int STAGE_BYTES = Cfg<NC>::STAGE_BYTES;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA destinations must be 128-byte aligned in shared memory
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int S = P.stages;
   unsigned char *stage_base = smem;
-  float4 *win = (float4 *)(smem + (size_t)S * STAGE_BYTES);  // [NSLOT][WIN]: rho, psi, psi^2, -
-  unsigned long long *bars = (unsigned long long *)(win + NSLOT * WIN);
+  float2 *win = (float2 *)(smem + (size_t)S * STAGE_BYTES);  // [NSLOT][WIN]: (psi, psi^2)
+  float *winr = (float *)(win + NSLOT * WIN);                // [NSLOT][WIN]: rho
+  unsigned long long *bars = (unsigned long long *)(winr + NSLOT * WIN);
   volatile int &s_abort = *(volatile int *)(bars + S);
 
   const int tid = threadIdx.x;
-  const bool consumer = tid < NCONS;
-  const int lane = tid & 31;
-  const bool producer = tid == NCONS;  // lane 0 of the last warp
+  const bool producer = tid == 0;
+  // the four top lanes of the last warp also form the halo columns:
+  // -1 and wr (always), -2 and wr+1 (rows whose ghost needs them)
+  const int hidx = tid - (NCONS - 4);
   const long long G = gridDim.x;
   const long long u0 = (long long)blockIdx.x * P.total / G;
   const long long u1 = (long long)(blockIdx.x + 1) * P.total / G;
@@ -352,21 +359,20 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_fused(const __grid_constant__ C
   int prev_stage = 0;
   int it = 0;
   bool bad = false;
-  // consumer t owns columns t and t + NCONS: unit-stride shared-memory and
-  // global accesses across the warp for each of the two
+  // thread t owns columns t, t + NCONS, ...: unit-stride shared-memory and
+  // global accesses across the warp for each of them
 
   while (cs.has) {
     const int v = cs.v;
     const int x0 = cs.strip * W;
     const int wr = min(W, P.nx - x0);
-    float4 *wcur = win + (size_t)(it & 3) * WIN;
+    float2 *wcur = win + (size_t)(it & 3) * WIN;
+    float *rcur = winr + (size_t)(it & 3) * WIN;
     const bool need2 = P.walls && geo && ((v == 1 && cs.ya == 1) || (v == P.ny - 2 && cs.yb == P.ny - 1));
-    // halo lanes: 0 -> c = -1, 1 -> c = wr, 2 -> c = -2, 3 -> c = wr + 1
-    const int hc = lane == 0 ? -1 : lane == 1 ? wr : lane == 2 ? -2 : wr + 1;
-    const bool hact = !consumer && (lane < 2 || (lane < 4 && need2));
-    const bool cact0 = consumer && tid < wr;
-    const bool cact1 = consumer && tid + NCONS < wr;
-    const bool cact = cact0;
+    const int hc = hidx == 0 ? -1 : hidx == 1 ? wr : hidx == 2 ? -2 : wr + 1;
+    const bool hact = hidx >= 0 && (hidx < 2 || need2);
+    const bool hact2 = hidx >= 0 && hidx < 2;  // halo columns that get a ghost value
+    const bool cact = tid < wr;
     int cur_stage = prev_stage;
     if (!cs.solid(P)) {
       const int s = get_stage;
@@ -381,64 +387,81 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_fused(const __grid_constant__ C
         atomicOr(P.flag + 1, 1);
       }
       const float *st = (const float *)(stage_base + (size_t)s * STAGE_BYTES);
-      if (cact) {
 #pragma unroll
-        for (int j = 0; j < NC; ++j) {
-          const int c = tid + j * NCONS;
-          if (j == 0 || cact1) {
-            const float *q = st + c;
-            float r = (((q[0] + q[W]) + (q[2 * W] + q[3 * W])) + ((q[4 * W] + q[5 * W]) + (q[6 * W] + q[7 * W]))) +
-                      q[8 * W];
-            wcur[c + 2] = eos_node(P, r);
-            bad |= !(r > 0.0f) || r > P.rho_max;
-          }
+      for (int j = 0; j < NC; ++j) {
+        const int c = tid + j * NCONS;
+        if (c < wr) {
+          const float *q = st + c;
+          float r = (((q[0] + q[W]) + (q[2 * W] + q[3 * W])) + ((q[4 * W] + q[5 * W]) + (q[6 * W] + q[7 * W]))) +
+                    q[8 * W];
+          const float4 e = eos_node(P, r);
+          rcur[c + 2] = r;
+          wcur[c + 2] = make_float2(e.y, e.z);
+          bad |= !(r > 0.0f) || r > P.rho_max;
         }
-      } else if (hact) {
+      }
+      if (hact) {
         const float *src = hc < 0 ? st + MAIN_BYTES / 4 + (HB + hc) : st + (MAIN_BYTES + HALO_PAD) / 4 + (hc - wr);
-        float r = 0.0f;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) r += src[a * HB];
-        wcur[hc + 2] = eos_node(P, r);
+        float r = (((src[0] + src[HB]) + (src[2 * HB] + src[3 * HB])) +
+                   ((src[4 * HB] + src[5 * HB]) + (src[6 * HB] + src[7 * HB]))) +
+                  src[8 * HB];
+        const float4 e = eos_node(P, r);
+        rcur[hc + 2] = r;
+        wcur[hc + 2] = make_float2(e.y, e.z);
       }
       ++consumed;
       // bottom ghost row (Eqs. 19-21): rows 1 and 2 are now in the window
       if (P.walls && geo && cs.ya == 1 && v == 2) {
-        const float4 *r1w = win + (size_t)((it - 1) & 3) * WIN;  // row 1
-        float4 *gw = win + (size_t)((it - 2) & 3) * WIN;         // row 0
-        if (cact) {
+        const float *r1w = winr + (size_t)((it - 1) & 3) * WIN;  // row 1 densities
+        float2 *gw = win + (size_t)((it - 2) & 3) * WIN;         // row 0
+        float *gr = winr + (size_t)((it - 2) & 3) * WIN;
 #pragma unroll
-          for (int j = 0; j < NC; ++j) {
-            const int c = tid + j * NCONS;
-            if (j == 0 || cact1) gw[c + 2] = ghost_node(P, r1w, wcur, c, x0 + c, 0);
+        for (int j = 0; j < NC; ++j) {
+          const int c = tid + j * NCONS;
+          if (c < wr) {
+            const float4 e = ghost_node(P, r1w, rcur, c, x0 + c, 0);
+            gr[c + 2] = e.x;
+            gw[c + 2] = make_float2(e.y, e.z);
           }
-        } else if (!consumer && lane < 2) {
+        }
+        if (hact2) {
           int gx = x0 + hc;
           gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-          gw[hc + 2] = ghost_node(P, r1w, wcur, hc, gx, 0);
+          const float4 e = ghost_node(P, r1w, rcur, hc, gx, 0);
+          gr[hc + 2] = e.x;
+          gw[hc + 2] = make_float2(e.y, e.z);
         }
       }
     } else {
       // solid row: zero potential (Martys-Chen), or the top ghost row from rows
       // ny-2 and ny-3 (the bottom ghost row is filled at v == 2)
       const bool top = v != 0;
-      const float4 *r1w = win + (size_t)((it - 1) & 3) * WIN;
-      const float4 *r2w = win + (size_t)((it - 2) & 3) * WIN;
-      if (cact) {
+      const float *r1w = winr + (size_t)((it - 1) & 3) * WIN;
+      const float *r2w = winr + (size_t)((it - 2) & 3) * WIN;
 #pragma unroll
-        for (int j = 0; j < NC; ++j) {
-          const int c = tid + j * NCONS;
-          if (j == 0 || cact1) {
-            if (!geo) wcur[c + 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            else if (top) wcur[c + 2] = ghost_node(P, r1w, r2w, c, x0 + c, 1);
+      for (int j = 0; j < NC; ++j) {
+        const int c = tid + j * NCONS;
+        if (c < wr) {
+          if (!geo) {
+            rcur[c + 2] = 0.0f;
+            wcur[c + 2] = make_float2(0.0f, 0.0f);
+          } else if (top) {
+            const float4 e = ghost_node(P, r1w, r2w, c, x0 + c, 1);
+            rcur[c + 2] = e.x;
+            wcur[c + 2] = make_float2(e.y, e.z);
           }
         }
-      } else if (!consumer && lane < 2) {
+      }
+      if (hact2) {
         if (!geo) {
-          wcur[hc + 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          rcur[hc + 2] = 0.0f;
+          wcur[hc + 2] = make_float2(0.0f, 0.0f);
         } else if (top) {
           int gx = x0 + hc;
           gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-          wcur[hc + 2] = ghost_node(P, r1w, r2w, hc, gx, 1);
+          const float4 e = ghost_node(P, r1w, r2w, hc, gx, 1);
+          rcur[hc + 2] = e.x;
+          wcur[hc + 2] = make_float2(e.y, e.z);
         }
       }
     }
@@ -448,9 +471,10 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_fused(const __grid_constant__ C
     // ---- collide row v-1 (its populations are still in stage prev_stage) ----
     if (cact && v >= cs.ya + 1 && v <= cs.yb) {
       const int y = v - 1;
-      const float4 *wm = win + (size_t)((it - 2) & 3) * WIN;  // row y-1
-      const float4 *w0 = win + (size_t)((it - 1) & 3) * WIN;  // row y
-      const float4 *wp = wcur;                                 // row y+1
+      const float2 *wm = win + (size_t)((it - 2) & 3) * WIN;  // row y-1
+      const float2 *w0 = win + (size_t)((it - 1) & 3) * WIN;  // row y
+      const float2 *wp = wcur;                                 // row y+1
+      const float *r0w = winr + (size_t)((it - 1) & 3) * WIN;
       const float *st = (const float *)(stage_base + (size_t)prev_stage * STAGE_BYTES);
       const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
       const bool wall_dn = P.walls && y == 1, wall_up = P.walls && y == P.ny - 2;
@@ -463,9 +487,9 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_fused(const __grid_constant__ C
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int c = tid + j * NCONS;
-        if (j == 1 && !cact1) break;
+        if (c >= wr) break;
         const int i0 = c + 2;
-        float4 nb[9];
+        float2 nb[9];
         nb[0] = w0[i0];
         nb[1] = w0[i0 + 1];
         nb[2] = wp[i0];
@@ -478,7 +502,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_fused(const __grid_constant__ C
         float f[9], fs[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) f[a] = st[a * W + c];
-        collide_node<UNIT>(P, f, nb, y, fs);
+        collide_node<UNIT>(P, f, nb, r0w[i0], y, fs);
         // streaming with half-way bounce-back
         const int x = x0 + c;
         const unsigned xm = x == 0 ? P.nx - 1 : x - 1, xp = x == P.nx - 1 ? 0 : x + 1;
@@ -550,8 +574,15 @@ bool encode(CUtensorMap *m, void *base, int nx, int ny, int boxw) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int NC>
 size_t smem_bytes(int stages) {
-  return 128 + (size_t)stages * STAGE_BYTES + (size_t)NSLOT * WIN * sizeof(float4) + (size_t)stages * 8 + 16;
+  return 128 + (size_t)stages * Cfg<NC>::STAGE_BYTES + (size_t)NSLOT * Cfg<NC>::WIN * (sizeof(float2) + sizeof(float)) +
+         (size_t)stages * 8 + 16;
+}
+
+const void *kernel_ptr(bool unit, int nc) {
+  if (nc == 1) return unit ? (const void *)k_fused<true, 1> : (const void *)k_fused<false, 1>;
+  return unit ? (const void *)k_fused<true, 2> : (const void *)k_fused<false, 2>;
 }
 
 }  // namespace
@@ -560,19 +591,23 @@ int lbm_fused_plan(lbm_ctx *C) {
   C->fused_ok = 0;
   if (C->precision != 32 || (C->nx % 4) != 0) return 0;
   static_assert(sizeof(CUtensorMap) <= sizeof(C->tmaps[0]), "tensor map storage");
+  // tuning knobs (defaults measured on GB300): columns per thread, TMA ring
+  // depth and CTAs per SM
+  int nc = 2;
+  if (const char *e = getenv("LBM_FUSED_COLS")) nc = atoi(e) == 1 ? 1 : 2;
+  int stages = 4;
+  if (const char *e = getenv("LBM_FUSED_STAGES")) stages = atoi(e);
+  if (stages < 3 || stages > 12) stages = 4;
+  const int W = nc * NCONS;
   for (int b = 0; b < 2; ++b) {
     if (!encode((CUtensorMap *)C->tmaps[2 * b], C->f[b], C->nx, C->ny, W)) return 0;
     if (!encode((CUtensorMap *)C->tmaps[2 * b + 1], C->f[b], C->nx, C->ny, HB)) return 0;
   }
-  // tuning knobs (defaults measured on GB300): TMA ring depth and CTAs per SM
-  int stages = 4;
-  if (const char *e = getenv("LBM_FUSED_STAGES")) stages = atoi(e);
-  if (stages < 3 || stages > 12) stages = 4;
-  size_t smem = smem_bytes(stages);
+  size_t smem = nc == 1 ? smem_bytes<1>(stages) : smem_bytes<2>(stages);
   // the diag(0,1,...,1) relaxation of Sec. 3.1 takes the specialised collision
   const lbm_dev_params &D = C->dp;
   C->fused_unit = D.s[1] == 1.0 && D.s[2] == 1.0 && D.s[4] == 1.0 && D.s[7] == 1.0;
-  const void *kern = C->fused_unit ? (const void *)k_fused<true> : (const void *)k_fused<false>;
+  const void *kern = kernel_ptr(C->fused_unit, nc);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -580,7 +615,7 @@ int lbm_fused_plan(lbm_ctx *C) {
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTHREADS, smem) != cudaSuccess || occ < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NCONS, smem) != cudaSuccess || occ < 1) {
     cudaGetLastError();
     return 0;
   }
@@ -593,6 +628,7 @@ int lbm_fused_plan(lbm_ctx *C) {
   }
   long long blocks = (long long)nsm * occ;
   if (blocks > total) blocks = total;
+  C->fused_cols = nc;
   C->tile_w = W;
   C->tile_stages = stages;
   C->tile_blocks = (int)blocks;
@@ -604,6 +640,7 @@ int lbm_fused_plan(lbm_ctx *C) {
 cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches) {
   FusedArgs P;
   const lbm_dev_params &D = C->dp;
+  const int W = C->tile_w;
   P.nx = C->nx;
   P.ny = C->ny;
   P.walls = C->walls;
@@ -643,10 +680,14 @@ cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches) {
   P.flag = C->d_flag;
   const CUtensorMap *tm = (const CUtensorMap *)C->tmaps[2 * src];
   const CUtensorMap *th = (const CUtensorMap *)C->tmaps[2 * src + 1];
-  if (C->fused_unit)
-    k_fused<true><<<C->tile_blocks, NTHREADS, C->fused_smem, C->stream>>>(*tm, *th, P);
-  else
-    k_fused<false><<<C->tile_blocks, NTHREADS, C->fused_smem, C->stream>>>(*tm, *th, P);
+  const dim3 grid(C->tile_blocks), block(NCONS);
+  if (C->fused_cols == 1) {
+    if (C->fused_unit) k_fused<true, 1><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
+    else k_fused<false, 1><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
+  } else {
+    if (C->fused_unit) k_fused<true, 2><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
+    else k_fused<false, 2><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
+  }
   ++*launches;
   return cudaGetLastError();
 }

@@ -56,6 +56,7 @@ struct lbm_ctx {
   int red_len;
   // fused kernel plan
   int fused_ok, fused_unit;  // fused kernel usable; unit-rate specialisation
+  int fused_cols;            // columns per thread of the fused kernel
   int tile_w, tile_blocks, tile_stages, fused_smem;
   unsigned char tmaps[4][128];   // CUtensorMap for f[0], f[1]: main box, halo box
 };
