@@ -247,6 +247,35 @@ int lbm_sync(lbm_ctx *ctx);
 /* Free everything the context owns (not a caller-owned state buffer). */
 void lbm_destroy(lbm_ctx *ctx);
 
+/* ---- allocation-free entry point ------------------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory: code that runs under another framework's allocator
+ * (which must own every device byte), embedders whose device allocation is
+ * disabled or budgeted to zero, and real-time loops where cudaMalloc's implicit
+ * synchronisation is not allowed.  It computes what lbm_mass computes -- the
+ * sum of rho = sum_a f_a over the fluid nodes -- directly from a
+ * distribution-function array the caller owns.
+ *
+ *  f:         device pointer, [9][ny][nx] floats (precision 32) or doubles (64);
+ *             rows 0 and ny-1 are skipped when walls = 1.
+ *  mass:      device pointer to one double that receives the result.
+ *  stream:    cudaStream_t the two kernels are queued on (NULL = legacy default);
+ *             the call returns once they are queued.
+ * Scratch: the block partial sums live in a fixed device array of
+ * LBM_NOALLOC_MAX_PARTIALS doubles (8 KiB), compiled into the library and held
+ * by every GPU that loads it until the process exits.  Every call on a device
+ * shares that array; it is fully rewritten by each call, so nothing carries
+ * over, but calls that overlap on the GPU (different streams) race on it.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  No device memory is allocated or freed.
+ * Errors: LBM_EINVAL for NULL pointers, precision not 32/64, walls not 0/1,
+ * too few rows, or nx * ny > LBM_NOALLOC_MAX_NODES; LBM_ECUDA if the lookup or
+ * a launch fails. */
+#define LBM_NOALLOC_MAX_PARTIALS 1024
+#define LBM_NOALLOC_MAX_NODES (1 << 28)
+int lbm_mass_noalloc(const void *f, int nx, int ny, int precision, int walls, double *mass, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,7 @@ UNITS = {
     "lbm_ref.cu": ["-fmad=false"],
     "lbm_measure.cu": ["-fmad=false"],
     "lbm_fused.cu": [],
+    "lbm_noalloc.cu": [],
 }
 HEADERS = [os.path.join(CSRC, "lbm_internal.h"), os.path.join(ROOT, "include", "lbm.h")]
 

@@ -104,6 +104,7 @@ _SIGS = {
     "lbm_launch_count": (ctypes.c_ulonglong, [c_void_p]),
     "lbm_sync": (c_int, [c_void_p]),
     "lbm_destroy": (None, [c_void_p]),
+    "lbm_mass_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
 }
 
 
@@ -339,6 +340,14 @@ def lbm_sync(ctx):
 def lbm_destroy(ctx):
     if ctx:
         load().lbm_destroy(ctx)
+
+
+def lbm_mass_noalloc(f_ptr, nx, ny, precision, walls, mass_ptr, stream=None):
+    """Sum of rho over the fluid nodes of a caller-owned device array f_ptr
+    ([9][ny][nx] of float32 or float64) into the device double at mass_ptr,
+    without allocating device memory (see lbm.h).  Pointers are ints."""
+    _check(load().lbm_mass_noalloc(c_void_p(f_ptr), nx, ny, precision, 1 if walls else 0, c_void_p(mass_ptr),
+                                   _stream_handle(stream)), "lbm_mass_noalloc")
 
 
 # ---- convenience wrapper ------------------------------------------------------
