@@ -2,7 +2,7 @@
 
 Default workload: the 4096 x 2048 large-density-ratio case -- the Eq. 11 EOS of
 Table 1 at density ratio 1000, the paper's relaxation (all rates 1), geometric
-wetting with 4 iterations, 64 seeded droplets (32 per wall, theta ~ U[30, 150]
+wetting with 4 iterations, 24 seeded droplets (12 per wall, theta ~ U[30, 150]
 deg), 5000 steps -- in FP32 with the fused kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -55,6 +55,26 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """Largest value of x over the ranks of the default process group (x itself
+    for a single process).  device: where the collective runs ("cuda" for NCCL,
+    "cpu" for gloo)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(ws: int, nodes_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank updates nodes_per_rank nodes per step
+    (independent replicas), and the job takes as long as its slowest rank."""
+    return ws * nodes_per_rank * steps / seconds / 1e6
 
 
 class ClockSampler:
@@ -278,13 +298,9 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     status = sim.status()
-    t_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, ws, "cuda")
     fluid = w.nx * (w.ny - 2)
-    value = ws * fluid * args.steps / (t_max * 1e-3) / 1e6
+    value = job_mlups(ws, fluid, args.steps, t_max * 1e-3)
     kernel_ms = ms / max(1, launches) if info.kernel_in_use == L.LBM_KERNEL_FUSED else None
 
     # ---- end to end through the C ABI with host buffers ---------------------
@@ -303,11 +319,8 @@ def run_ours(args):
     barrier()
     e2e_s = time.perf_counter() - t0
     sim2.close()
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = ws * fluid * args.steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(e2e_s, ws, "cuda")
+    e2e = job_mlups(ws, fluid, args.steps, e2e_s)
     node_bytes = 8 * w.nx * w.ny
 
     if rank == 0:
