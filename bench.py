@@ -374,8 +374,9 @@ def _kernel_sha():
     import hashlib
 
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1501_05430_gb300", "csrc", "lbm_fused.cu"), "rb") as fh:
-        h.update(fh.read())
+    for name in ("lbm_fused.cu", "lbm_node.cuh"):
+        with open(os.path.join(ROOT, "paper_1501_05430_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -276,6 +276,100 @@ void lbm_destroy(lbm_ctx *ctx);
 #define LBM_NOALLOC_MAX_NODES (1 << 28)
 int lbm_mass_noalloc(const void *f, int nx, int ny, int precision, int walls, double *mass, void *stream);
 
+/* ---- batched sweep ----------------------------------------------------- *
+ * Many independent droplet instances -- each with its own grid size, EOS
+ * temperature, relaxation rates and wall-angle field -- advanced together by
+ * one persistent kernel per launch (the contact-angle x density-ratio sweeps
+ * of Secs. 3.1 and 4.2 run as one job instead of one solver per case).
+ *
+ * Every instance has solid rows at y = 0 and y = ny-1, precision 32, and
+ * nx a multiple of 4.  Its state lives in one device pool owned by the batch.
+ * Each instance is cut into work items (bands of whole fluid rows); one launch
+ * advances every instance by steps_per_launch steps, and the CTAs that share
+ * an instance meet at a per-instance barrier between its steps (no barrier
+ * across instances).  Per node the arithmetic is that of lbm_step's FP32
+ * kernel, so the per-instance results agree with a lone context to FP32
+ * rounding. */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct {
+  int nx, ny;            /* grid; rows 0 and ny-1 solid; nx % 4 == 0 */
+  lbm_eos eos;
+  double T, tau;         /* as for lbm_create */
+  const double *theta;   /* [ny][nx] radians (rows 0 and ny-1 read) or NULL = pi/2 */
+  lbm_params params;     /* precision must be 32; kernel is ignored */
+} lbm_instance_desc;
+
+/* Launch shape.  Zero fields take the defaults in brackets. */
+typedef struct {
+  int threads;           /* threads per CTA, 128 or 256 [128; 256 when some nx > 512];
+                            columns per thread = ceil(nx / threads) <= 4 */
+  int ctas_per_sm;       /* cap on resident CTAs per SM [occupancy maximum] */
+  int stages;            /* row stages of the shared-memory copy ring, 3..6 [4] */
+  int band_rows[4];      /* fluid rows per work item for nx in (0,128], (128,256],
+                            (256,384], (384, ...) [32 each] */
+  int steps_per_launch;  /* steps advanced by one launch [16] */
+  int graph_launches;    /* launches captured per CUDA graph and replayed [0 = no graph];
+                            used when graph_launches * steps_per_launch is even and the
+                            batch has a non-NULL stream */
+  double wait_seconds;   /* bound on every barrier wait [2 s], at most 60 */
+  int hold_instance;     /* testing aid, -1 normally: the given instance's first work
+                            item never arrives at its barrier, so the other items of
+                            that instance wait until wait_seconds runs out */
+} lbm_batch_config;
+
+int lbm_batch_config_default(lbm_batch_config *cfg);
+
+/* Create n instances.  inst[i].theta is copied.  cfg may be NULL (defaults).
+ * stream: cudaStream_t for all the batch's work (NULL = legacy default; CUDA
+ * graphs need a non-NULL stream).  Each instance starts with f = 0; set it
+ * with lbm_set_rho / lbm_init_droplets / lbm_set_f on lbm_batch_instance().
+ * Errors: LBM_EINVAL (n < 1, an instance's sizes, precision or parameters),
+ * LBM_EUNSUPPORTED (nx > 4 * threads), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_batch_create(int n, const lbm_instance_desc *inst, const lbm_batch_config *cfg, void *stream,
+                     lbm_batch **out);
+int lbm_batch_size(const lbm_batch *b);
+
+/* The context of instance i, owned by the batch (never lbm_destroy it).  Every
+ * lbm_* call works on it (setters, getters, measurements, checkpoints, even
+ * lbm_step for that instance alone); it shares the batch's stream.  NULL if i
+ * is out of range. */
+lbm_ctx *lbm_batch_instance(lbm_batch *b, int i);
+
+/* Advance every instance by nsteps.  Returns LBM_OK, LBM_ETIMEOUT if a
+ * barrier wait ran out (the batch is then failed for good; the instances
+ * concerned report LBM_ETIMEOUT), or LBM_ECUDA.  An instance that becomes
+ * unstable is flagged (its lbm_status() returns LBM_EUNSTABLE) and left
+ * frozen while the others go on; the call still returns LBM_OK.
+ * Synchronises the stream before it returns. */
+int lbm_batch_step(lbm_batch *b, int nsteps);
+
+/* Batch status (LBM_OK or LBM_ETIMEOUT); inst_status[n] (may be NULL)
+ * receives each instance's status. */
+int lbm_batch_status(lbm_batch *b, int *inst_status);
+
+/* Apparent contact angle of every instance on one wall over its full width
+ * (as lbm_contact_angle).  theta[n] required; H, L, status may be NULL.
+ * status[i] = LBM_OK or LBM_ENOCONTACT (theta[i] = NaN then). */
+int lbm_batch_contact_angles(lbm_batch *b, int wall, double *theta, double *H, double *L, int *status);
+
+/* Pick the launch shape by timing trial_steps steps of candidate
+ * configurations on a copy of the current state (threads x stages, then the
+ * band height of each size class present, then steps_per_launch), install the
+ * fastest and put the state back.  best (may be NULL) receives it.
+ * Needs one extra state-sized device allocation while it runs. */
+int lbm_batch_autotune(lbm_batch *b, int trial_steps, lbm_batch_config *best);
+
+int lbm_batch_get_config(const lbm_batch *b, lbm_batch_config *cfg);
+/* Install a launch shape (validated as in lbm_batch_create). */
+int lbm_batch_set_config(lbm_batch *b, const lbm_batch_config *cfg);
+/* Plan of the current shape: CTAs per launch, work items, dynamic shared
+ * memory per CTA, resident CTAs per SM.  Any pointer may be NULL. */
+int lbm_batch_get_plan(const lbm_batch *b, int *grid, int *items, int *smem_bytes, int *ctas_per_sm);
+/* Kernel launches issued by lbm_batch_step so far (graph replays included). */
+unsigned long long lbm_batch_launch_count(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

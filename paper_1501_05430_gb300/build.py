@@ -3,7 +3,8 @@
 Translation units and their floating-point flags:
   lbm_ref.cu, lbm_measure.cu  -fmad=false: the canonical-order kernels must not
                                contract a*b+c into an FMA (bit-exact FP64 path)
-  lbm_fused.cu                 FMA allowed: the production FP32 step
+  lbm_fused.cu, lbm_batch.cu   FMA allowed: the production FP32 step (one domain; many
+                               instances in one persistent launch)
   lbm_api.cu                   host code and launch orchestration
 Units compile in parallel; only stale objects are rebuilt.
 """
@@ -25,8 +26,9 @@ UNITS = {
     "lbm_measure.cu": ["-fmad=false"],
     "lbm_fused.cu": [],
     "lbm_noalloc.cu": [],
+    "lbm_batch.cu": [],
 }
-HEADERS = [os.path.join(CSRC, "lbm_internal.h"), os.path.join(ROOT, "include", "lbm.h")]
+HEADERS = [os.path.join(CSRC, "lbm_internal.h"), os.path.join(CSRC, "lbm_node.cuh"), os.path.join(ROOT, "include", "lbm.h")]
 
 
 def _nvcc() -> str:

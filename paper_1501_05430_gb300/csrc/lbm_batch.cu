@@ -1,0 +1,925 @@
+// lbm_batch.cu -- many independent droplet instances (uneven nx, ny, EOS
+// temperature, tau, wall angles) advanced together by one persistent launch.
+//
+// Work list: every instance is cut into "items", bands of whole fluid rows
+// (full width, so the periodic x neighbours are in the CTA's own window).  The
+// items of all instances form one list, ordered by instance and row; the host
+// splits it into one contiguous, cost-balanced range per CTA.  A launch runs
+// `steps` timesteps.  Between two steps of the same instance the CTAs that own
+// its items meet at a per-instance barrier: a global arrival counter, released
+// with a fence + atomic add, acquired with a bounded spin on %globaltimer.  A
+// wait that runs out sets a per-instance timeout bit and a batch abort word,
+// and every CTA leaves at its next item.  Instances never wait on each other,
+// so a small instance owned by one CTA never synchronises beyond its CTA.
+//
+// Rows are streamed through a ring of shared-memory stages with 16-byte
+// cp.async copies that bypass L1 (.cg), so rows written by other CTAs in the
+// previous step are read from L2 after the barrier's acquire.  Per row the
+// node arithmetic is the one of the single-domain fused kernel
+// (lbm_node.cuh): rho, EOS, ghost rows (Eqs. 19-21), force (Eq. 9, Eq. 14),
+// Eq. 17 tensor, MRT collision with the Eq. 6 forcing and Eq. 16 source, push
+// streaming with half-way bounce-back.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "lbm_internal.h"
+#include "lbm_node.cuh"
+
+namespace {
+
+using lbm_node::collide_node;
+using lbm_node::eos_node;
+using lbm_node::ghost_node;
+
+constexpr int kMaxCpt = 4;  // columns per thread: nx <= 4 x threads per CTA
+constexpr int kSlots = 4;   // window rows (ring)
+
+// Per-instance block: the node-function fields (same names as the fused
+// kernel's) and the batch bookkeeping.
+struct BInst {
+  int kind, wetting, walls, nx, ny, n_iter;
+  float b4, RT, a, r1, r2, pc0, pc1, pc2;
+  float A, omA, pre, halfA, rho_max, ghost_max;
+  float se, seps, sq, snu, he, heps, hq, hnu, Gw;
+  const double *coef;
+  int unit;    // all non-conserved rates are 1
+  int items;   // items of this instance = barrier arrivals per step
+  int first;   // index of its first item
+  int pad;
+  float *f[2];
+  int *flag;   // the instance context's flags: [0] unstable, [1] timeout
+};
+
+struct BItem {
+  int inst, y0, y1, pad;  // fluid rows [y0, y1)
+};
+
+struct BatchArgs {
+  const BInst *inst;
+  const BItem *items;
+  const int *cta_first;    // [grid + 1]
+  unsigned *bar;           // [ninst] arrivals in this launch (zeroed before it)
+  int *abort;              // [0]: a barrier wait ran out
+  int *iflag;              // [ninst] bit 0 unstable, bit 1 timeout
+  const int *cur;          // [ninst] array index holding the state at phase 0
+  int steps, phase;        // steps in this launch; parity of its first step
+  int nxs, stages;         // stage row stride (floats), ring depth
+  unsigned long long wait_ns;
+  int hold;                // testing aid: this instance's first item never arrives (-1: none)
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void cp16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_wait_dyn(int pending) {
+  // pending = stages - 3 in [0, 3]
+  if (pending <= 0) cp_wait<0>();
+  else if (pending == 1) cp_wait<1>();
+  else if (pending == 2) cp_wait<2>();
+  else cp_wait<3>();
+}
+
+// Bounded wait until *p >= target.  False if the batch aborted or the wait ran out.
+__device__ bool wait_ge(const unsigned *p, unsigned target, const int *abort, unsigned long long limit) {
+  if (ld_acquire(p) >= target) return true;
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    __nanosleep(200);
+    if (ld_acquire(p) >= target) return true;
+    if (*(volatile const int *)abort) return false;
+    if (gtimer() - t0 > limit) return false;
+  }
+}
+
+// One item of one step: stream virtual rows y0-1 .. y1 (halo and solid rows
+// included), fill the window, collide rows y0 .. y1-1 into dst.
+template <bool UNIT, int NT>
+__device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__ src, float *__restrict__ dst,
+                      float *stage, float2 *win, float *winr, int nxs, int S, bool &bad) {
+  const int tid = threadIdx.x;
+  const int nx = P.nx, ny = P.ny, nx4 = nx >> 2;
+  const size_t n = (size_t)nx * ny;
+  const int wn = nxs + 4;  // window row: column c at c + 2
+  const int R = it.y1 - it.y0 + 2;
+  const bool geo = P.wetting == LBM_WET_GEOMETRIC;
+  const int stage_floats = 9 * nxs;
+
+  auto issue = [&](int j) {
+    const int v = it.y0 - 1 + j;
+    if (v <= 0 || v >= ny - 1) return;  // solid rows are not loaded
+    float *st = stage + (size_t)(j % S) * stage_floats;
+    const float *row = src + (size_t)v * nx;
+    for (int q = tid; q < 9 * nx4; q += NT) {
+      const int a = q / nx4, c4 = q - a * nx4;
+      cp16(st + a * nxs + 4 * c4, row + a * n + 4 * c4);
+    }
+  };
+  for (int j = 0; j < S - 2; ++j) {
+    if (j < R) issue(j);
+    cp_commit();
+  }
+
+  for (int j = 0; j < R; ++j) {
+    const int v = it.y0 - 1 + j;
+    cp_wait_dyn(S - 3);
+    __syncthreads();  // row j staged by every thread; row j-2's stage and window slot j-4 are free
+    if (j + S - 2 < R) issue(j + S - 2);
+    cp_commit();
+
+    float2 *wcur = win + (size_t)(j & 3) * wn;
+    float *rcur = winr + (size_t)(j & 3) * wn;
+    const bool solid = v == 0 || v == ny - 1;
+    if (!solid) {
+      const float *st = stage + (size_t)(j % S) * stage_floats;
+#pragma unroll
+      for (int k = 0; k < kMaxCpt; ++k) {
+        const int c = tid + k * NT;
+        if (c < nx) {
+          const float *q = st + c;
+          const float r = (((q[0] + q[nxs]) + (q[2 * nxs] + q[3 * nxs])) +
+                           ((q[4 * nxs] + q[5 * nxs]) + (q[6 * nxs] + q[7 * nxs]))) +
+                          q[8 * nxs];
+          const float4 e = eos_node(P, r);
+          const float2 pe = make_float2(e.y, e.z);
+          rcur[c + 2] = r;
+          wcur[c + 2] = pe;
+          if (c == nx - 1) { rcur[1] = r; wcur[1] = pe; }
+          if (c == 0) { rcur[nx + 2] = r; wcur[nx + 2] = pe; }
+          bad |= !(r > 0.0f) || r > P.rho_max;
+        }
+      }
+      // bottom ghost row (Eqs. 19-21) once rows 1 and 2 are in the window
+      if (geo && it.y0 == 1 && v == 2) {
+        const float *r1w = winr + (size_t)((j - 1) & 3) * wn;
+        float2 *gw = win + (size_t)((j - 2) & 3) * wn;
+        float *gr = winr + (size_t)((j - 2) & 3) * wn;
+#pragma unroll
+        for (int k = 0; k < kMaxCpt; ++k) {
+          const int c = tid + k * NT;
+          if (c < nx) {
+            const float4 e = ghost_node(P, r1w, rcur, c, c, 0);
+            const float2 pe = make_float2(e.y, e.z);
+            gr[c + 2] = e.x;
+            gw[c + 2] = pe;
+            if (c == nx - 1) { gr[1] = e.x; gw[1] = pe; }
+            if (c == 0) { gr[nx + 2] = e.x; gw[nx + 2] = pe; }
+          }
+        }
+      }
+    } else if (!geo || v == ny - 1) {
+      // Martys-Chen: solid rows carry psi = U = 0.  Geometric: the top ghost
+      // row from rows ny-2 and ny-3 (the bottom one is filled at v == 2).
+      const float *r1w = winr + (size_t)((j - 1) & 3) * wn;
+      const float *r2w = winr + (size_t)((j - 2) & 3) * wn;
+#pragma unroll
+      for (int k = 0; k < kMaxCpt; ++k) {
+        const int c = tid + k * NT;
+        if (c < nx) {
+          float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if (geo) e = ghost_node(P, r1w, r2w, c, c, 1);
+          const float2 pe = make_float2(e.y, e.z);
+          rcur[c + 2] = e.x;
+          wcur[c + 2] = pe;
+          if (c == nx - 1) { rcur[1] = e.x; wcur[1] = pe; }
+          if (c == 0) { rcur[nx + 2] = e.x; wcur[nx + 2] = pe; }
+        }
+      }
+    }
+    __syncthreads();  // window row j complete
+
+    // ---- collide row v-1 (its populations are in the stage of row j-1) ----
+    const int y = v - 1;
+    if (j >= 1 && y >= it.y0 && y < it.y1) {
+      const float2 *wm = win + (size_t)((j - 2) & 3) * wn;
+      const float2 *w0 = win + (size_t)((j - 1) & 3) * wn;
+      const float2 *wp = wcur;
+      const float *r0w = winr + (size_t)((j - 1) & 3) * wn;
+      const float *st = stage + (size_t)((j - 1) % S) * stage_floats;
+      const bool wall_dn = y == 1, wall_up = y == ny - 2;
+      const size_t ry = (size_t)y * nx, rym = ry - nx, ryp = ry + nx;
+#pragma unroll
+      for (int k = 0; k < kMaxCpt; ++k) {
+        const int c = tid + k * NT;
+        if (c >= nx) break;
+        const int i0 = c + 2;
+        float2 nb[9];
+        nb[0] = w0[i0];
+        nb[1] = w0[i0 + 1];
+        nb[2] = wp[i0];
+        nb[3] = w0[i0 - 1];
+        nb[4] = wm[i0];
+        nb[5] = wp[i0 + 1];
+        nb[6] = wp[i0 - 1];
+        nb[7] = wm[i0 - 1];
+        nb[8] = wm[i0 + 1];
+        float f[9], fs[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) f[a] = st[a * nxs + c];
+        collide_node<UNIT>(P, f, nb, r0w[i0], y, fs);
+        const int x = c;
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        dst[ry + x] = fs[0];
+        dst[n + ry + xp] = fs[1];
+        dst[3 * n + ry + xm] = fs[3];
+        if (wall_up) {
+          dst[4 * n + ry + x] = fs[2];
+          dst[7 * n + ry + x] = fs[5];
+          dst[8 * n + ry + x] = fs[6];
+        } else {
+          dst[2 * n + ryp + x] = fs[2];
+          dst[5 * n + ryp + xp] = fs[5];
+          dst[6 * n + ryp + xm] = fs[6];
+        }
+        if (wall_dn) {
+          dst[2 * n + ry + x] = fs[4];
+          dst[5 * n + ry + x] = fs[7];
+          dst[6 * n + ry + x] = fs[8];
+        } else {
+          dst[4 * n + rym + x] = fs[4];
+          dst[7 * n + rym + xm] = fs[7];
+          dst[8 * n + rym + xp] = fs[8];
+        }
+      }
+    }
+  }
+  cp_wait<0>();  // no copy of this item stays in flight into the next one's stages
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
+  extern __shared__ __align__(16) float smem_f[];
+  __shared__ BInst sP;
+  __shared__ int s_go, s_skip, s_bad;
+  const int S = A.stages, nxs = A.nxs;
+  float *stage = smem_f;
+  float2 *win = (float2 *)(stage + (size_t)S * 9 * nxs);
+  float *winr = (float *)(win + (size_t)kSlots * (nxs + 4));
+  const int tid = threadIdx.x;
+  const int i0 = A.cta_first[blockIdx.x], i1 = A.cta_first[blockIdx.x + 1];
+
+  for (int s = 0; s < A.steps; ++s) {
+    for (int ii = i0; ii < i1; ++ii) {
+      const BItem it = A.items[ii];
+      if (tid == 0) {
+        int go = 1;
+        if (*(volatile int *)A.abort) go = 0;
+        const BInst *gp = A.inst + it.inst;
+        if (go && s > 0) {
+          // every item of the instance has finished step s-1 of this launch
+          if (!wait_ge(A.bar + it.inst, (unsigned)(s * gp->items), A.abort, A.wait_ns)) {
+            if (!*(volatile int *)A.abort) {
+              atomicOr(A.iflag + it.inst, 2);
+              atomicOr(gp->flag + 1, 1);
+            }
+            atomicExch(A.abort, 1);
+            go = 0;
+          }
+        }
+        s_go = go;
+        s_bad = 0;
+        // a blown-up instance is carried along (its barriers still count), not computed
+        s_skip = *(volatile const int *)(A.iflag + it.inst) & 1;
+        if (go) sP = *gp;
+      }
+      __syncthreads();
+      if (!s_go) return;
+      const int par = A.cur[it.inst] ^ ((A.phase + s) & 1);
+      bool bad = false;
+      if (!s_skip) {
+        if (sP.unit)
+          sweep<true, NT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, winr, nxs, S, bad);
+        else
+          sweep<false, NT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, winr, nxs, S, bad);
+      }
+      if (bad) s_bad = 1;
+      __syncthreads();  // every store of the item issued
+      if (tid == 0) {
+        if (s_bad) {
+          atomicOr(A.iflag + it.inst, 1);
+          atomicOr(sP.flag, 1);
+        }
+        if (!(it.inst == A.hold && ii == sP.first)) {
+          __threadfence();
+          atomicAdd(A.bar + it.inst, 1u);
+        }
+      }
+    }
+  }
+}
+
+const void *kernel_ptr(int nt) { return nt == 256 ? (const void *)k_batch<256> : (const void *)k_batch<128>; }
+
+size_t smem_bytes(int nxs, int stages) {
+  return (size_t)stages * 9 * nxs * sizeof(float) + (size_t)kSlots * (nxs + 4) * (sizeof(float2) + sizeof(float));
+}
+
+int size_class(int nx) { return nx <= 128 ? 0 : nx <= 256 ? 1 : nx <= 384 ? 2 : 3; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct lbm_batch {
+  int n;
+  cudaStream_t stream;
+  lbm_batch_config cfg;
+  std::vector<lbm_ctx *> ctx;
+  void *pool;                 // every instance's two distribution arrays
+  size_t pool_bytes;
+  std::vector<size_t> offset; // byte offset of each instance's state in the pool
+  std::vector<BInst> hinst;
+  std::vector<BItem> items;
+  std::vector<int> cta_first;
+  std::vector<int> hcur;      // array index of each instance's state at phase 0
+  int phase;                  // steps since hcur was uploaded, mod 2
+  BInst *d_inst;
+  BItem *d_items;
+  int *d_cta_first;
+  unsigned *d_bar;
+  int *d_abort;
+  int *d_iflag;
+  int *d_cur;
+  size_t d_items_cap, d_cta_cap;
+  int grid, nxs, smem, occ, nsm;
+  cudaGraphExec_t graph[2];   // per starting phase
+  int graph_steps;
+  unsigned long long launches;
+  long long steps;
+  int status;
+};
+
+namespace {
+
+#define BCK(x)                          \
+  do {                                  \
+    if ((x) != cudaSuccess) {           \
+      cudaGetLastError();               \
+      return LBM_ECUDA;                 \
+    }                                   \
+  } while (0)
+
+void drop_graphs(lbm_batch *B) {
+  for (int p = 0; p < 2; ++p)
+    if (B->graph[p]) {
+      cudaGraphExecDestroy(B->graph[p]);
+      B->graph[p] = nullptr;
+    }
+  B->graph_steps = 0;
+}
+
+int resolve_config(const lbm_batch *B, const lbm_batch_config *in, lbm_batch_config *out) {
+  lbm_batch_config c = *in;
+  int nxmax = 0;
+  for (int i = 0; i < B->n; ++i) nxmax = std::max(nxmax, B->ctx[i]->nx);
+  if (c.threads == 0) c.threads = nxmax > 512 ? 256 : 128;
+  if (c.threads != 128 && c.threads != 256) return LBM_EINVAL;
+  if (nxmax > kMaxCpt * c.threads) return LBM_EUNSUPPORTED;
+  if (c.stages == 0) c.stages = 4;
+  if (c.stages < 3 || c.stages > 6) return LBM_EINVAL;
+  for (int k = 0; k < 4; ++k) {
+    if (c.band_rows[k] == 0) c.band_rows[k] = 32;
+    if (c.band_rows[k] < 1) return LBM_EINVAL;
+  }
+  if (c.steps_per_launch == 0) c.steps_per_launch = 16;
+  if (c.steps_per_launch < 1) return LBM_EINVAL;
+  if (c.graph_launches < 0 || c.ctas_per_sm < 0) return LBM_EINVAL;
+  if (c.wait_seconds == 0.0) c.wait_seconds = 2.0;
+  if (!(c.wait_seconds > 0.0) || c.wait_seconds > 60.0) return LBM_EINVAL;
+  if (c.hold_instance < -1 || c.hold_instance >= B->n) return LBM_EINVAL;
+  *out = c;
+  return LBM_OK;
+}
+
+// Items, CTA ranges, launch shape for B->cfg; uploads the tables.
+int plan(lbm_batch *B) {
+  const lbm_batch_config &c = B->cfg;
+  B->items.clear();
+  std::vector<double> cost;
+  int nxmax = 0;
+  for (int i = 0; i < B->n; ++i) {
+    const lbm_ctx *C = B->ctx[i];
+    nxmax = std::max(nxmax, C->nx);
+    const int band = c.band_rows[size_class(C->nx)];
+    B->hinst[i].first = (int)B->items.size();
+    int cnt = 0;
+    for (int y = 1; y < C->ny - 1; y += band) {
+      BItem it{i, y, std::min(y + band, C->ny - 1), 0};
+      B->items.push_back(it);
+      cost.push_back((double)(it.y1 - it.y0 + 2) * C->nx);  // two halo rows per item
+      ++cnt;
+    }
+    B->hinst[i].items = cnt;
+  }
+  B->nxs = (nxmax + 3) & ~3;
+  B->smem = (int)smem_bytes(B->nxs, c.stages);
+  const void *kern = kernel_ptr(c.threads);
+  BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, B->smem));
+  int dev = 0, occ = 0;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, dev));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, c.threads, B->smem));
+  if (occ < 1) return LBM_EUNSUPPORTED;
+  if (c.ctas_per_sm > 0 && c.ctas_per_sm < occ) occ = c.ctas_per_sm;
+  B->occ = occ;
+  const int nitems = (int)B->items.size();
+  int grid = std::min(B->nsm * occ, nitems);
+  // contiguous ranges of about equal cost
+  double total = 0;
+  for (double w : cost) total += w;
+  B->cta_first.assign(grid + 1, nitems);
+  B->cta_first[0] = 0;
+  double acc = 0;
+  int b = 1;
+  for (int k = 0; k < nitems && b < grid; ++k) {
+    acc += cost[k];
+    while (b < grid && acc >= total * b / grid) B->cta_first[b++] = k + 1;
+  }
+  // drop CTAs left without items
+  std::vector<int> cf;
+  cf.push_back(0);
+  for (int k = 1; k <= grid; ++k)
+    if (B->cta_first[k] > cf.back()) cf.push_back(B->cta_first[k]);
+  if (cf.back() != nitems) cf.push_back(nitems);
+  B->cta_first = cf;
+  B->grid = (int)cf.size() - 1;
+  // upload
+  if ((size_t)nitems > B->d_items_cap) {
+    cudaFree(B->d_items);
+    B->d_items = nullptr;
+    BCK(cudaMalloc(&B->d_items, (size_t)nitems * sizeof(BItem)));
+    B->d_items_cap = nitems;
+  }
+  if (B->cta_first.size() > B->d_cta_cap) {
+    cudaFree(B->d_cta_first);
+    B->d_cta_first = nullptr;
+    BCK(cudaMalloc(&B->d_cta_first, B->cta_first.size() * sizeof(int)));
+    B->d_cta_cap = B->cta_first.size();
+  }
+  BCK(cudaMemcpyAsync(B->d_items, B->items.data(), (size_t)nitems * sizeof(BItem), cudaMemcpyHostToDevice,
+                      B->stream));
+  BCK(cudaMemcpyAsync(B->d_cta_first, B->cta_first.data(), B->cta_first.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, B->stream));
+  BCK(cudaMemcpyAsync(B->d_inst, B->hinst.data(), (size_t)B->n * sizeof(BInst), cudaMemcpyHostToDevice, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  drop_graphs(B);
+  return LBM_OK;
+}
+
+// One launch of `steps` steps starting at parity `phase` (no synchronisation).
+int launch(lbm_batch *B, int steps, int phase) {
+  BatchArgs A;
+  A.inst = B->d_inst;
+  A.items = B->d_items;
+  A.cta_first = B->d_cta_first;
+  A.bar = B->d_bar;
+  A.abort = B->d_abort;
+  A.iflag = B->d_iflag;
+  A.cur = B->d_cur;
+  A.steps = steps;
+  A.phase = phase;
+  A.nxs = B->nxs;
+  A.stages = B->cfg.stages;
+  A.wait_ns = (unsigned long long)(B->cfg.wait_seconds * 1e9);
+  A.hold = B->cfg.hold_instance;
+  BCK(cudaMemsetAsync(B->d_bar, 0, (size_t)B->n * sizeof(unsigned), B->stream));
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(B->grid);
+  lc.blockDim = dim3(B->cfg.threads);
+  lc.dynamicSmemBytes = B->smem;
+  lc.stream = B->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the barriers need it
+  at[0].val.cooperative = 1;
+  lc.attrs = at;
+  lc.numAttrs = steps > 1 ? 1 : 0;
+  cudaError_t e = B->cfg.threads == 256 ? cudaLaunchKernelEx(&lc, k_batch<256>, A) : cudaLaunchKernelEx(&lc, k_batch<128>, A);
+  BCK(e);
+  ++B->launches;
+  return LBM_OK;
+}
+
+int sync_cur(lbm_batch *B) {
+  bool same = true;
+  for (int i = 0; i < B->n; ++i)
+    if (B->ctx[i]->cur != (B->hcur[i] ^ B->phase)) same = false;
+  if (same) return LBM_OK;
+  for (int i = 0; i < B->n; ++i) B->hcur[i] = B->ctx[i]->cur;
+  B->phase = 0;
+  BCK(cudaMemcpyAsync(B->d_cur, B->hcur.data(), (size_t)B->n * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  return LBM_OK;
+}
+
+int read_batch_flags(lbm_batch *B) {
+  std::vector<int> fl(B->n);
+  int ab = 0;
+  BCK(cudaMemcpyAsync(fl.data(), B->d_iflag, (size_t)B->n * sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+  BCK(cudaMemcpyAsync(&ab, B->d_abort, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  for (int i = 0; i < B->n; ++i) {
+    if (fl[i] & 2) B->ctx[i]->status = LBM_ETIMEOUT;
+    else if (fl[i] & 1) B->ctx[i]->status = LBM_EUNSTABLE;
+  }
+  if (ab) B->status = LBM_ETIMEOUT;
+  return B->status;
+}
+
+void fill_inst(BInst &I, const lbm_ctx *C, int *flag) {
+  const lbm_dev_params &D = C->dp;
+  memset(&I, 0, sizeof(I));
+  I.kind = D.eos_kind;
+  I.wetting = D.wetting;
+  I.walls = 1;
+  I.nx = C->nx;
+  I.ny = C->ny;
+  I.n_iter = D.n_iter;
+  I.b4 = (float)(0.25 * D.b);
+  I.RT = (float)(D.R * D.T);
+  I.a = (float)D.a;
+  I.r1 = (float)D.r1;
+  I.r2 = (float)D.r2;
+  I.pc0 = (float)(-2.0 * (D.thv - 1.0 / 3.0));
+  I.pc1 = (float)(-2.0 * (D.thm - D.thv));
+  I.pc2 = (float)(-2.0 * (D.thl - D.thm));
+  I.A = (float)D.A;
+  I.omA = (float)(1.0 - D.A);
+  I.pre = (float)(-0.5 * D.kappa);
+  I.halfA = (float)(0.5 * D.A);
+  I.rho_max = (float)fmin(D.rho_max, 3.0e38);
+  I.ghost_max = (float)fmin(D.ghost_max, 3.0e38);
+  I.se = (float)D.s[1];
+  I.seps = (float)D.s[2];
+  I.sq = (float)D.s[4];
+  I.snu = (float)D.s[7];
+  I.he = (float)(1.0 - 0.5 * D.s[1]);
+  I.heps = (float)(1.0 - 0.5 * D.s[2]);
+  I.hq = (float)(1.0 - 0.5 * D.s[4]);
+  I.hnu = (float)(1.0 - 0.5 * D.s[7]);
+  I.Gw = (float)D.Gw;
+  I.coef = C->d_coef;
+  I.unit = D.s[1] == 1.0 && D.s[2] == 1.0 && D.s[4] == 1.0 && D.s[7] == 1.0;
+  I.f[0] = (float *)C->f[0];
+  I.f[1] = (float *)C->f[1];
+  I.flag = flag;
+}
+
+int run_steps(lbm_batch *B, int nsteps) {
+  const int k = B->cfg.steps_per_launch;
+  const int G = B->cfg.graph_launches;
+  int done = 0;
+  // whole graphs (an even number of steps each, so a replay ends on the phase it started from)
+  if (G > 0 && B->stream && (long long)G * k % 2 == 0 && nsteps >= G * k) {
+    const int p = B->phase;
+    if (!B->graph[p]) {
+      cudaGraph_t g = nullptr;
+      BCK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+      int st = LBM_OK;
+      for (int l = 0; l < G && st == LBM_OK; ++l) st = launch(B, k, p ^ (l * k & 1));
+      cudaError_t e = cudaStreamEndCapture(B->stream, &g);
+      if (st != LBM_OK || e != cudaSuccess) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return LBM_ECUDA;
+      }
+      B->launches -= G;  // counted when replayed
+      e = cudaGraphInstantiate(&B->graph[p], g, 0);
+      cudaGraphDestroy(g);
+      BCK(e);
+      B->graph_steps = G * k;
+    }
+    while (nsteps - done >= B->graph_steps) {
+      BCK(cudaGraphLaunch(B->graph[p], B->stream));
+      B->launches += G;
+      done += B->graph_steps;
+    }
+  }
+  while (done < nsteps) {
+    const int m = std::min(k, nsteps - done);
+    int st = launch(B, m, (B->phase + done) & 1);
+    if (st) return st;
+    done += m;
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_config_default(lbm_batch_config *c) {
+  if (!c) return LBM_EINVAL;
+  memset(c, 0, sizeof(*c));
+  c->hold_instance = -1;
+  return LBM_OK;
+}
+
+int lbm_batch_create(int n, const lbm_instance_desc *inst, const lbm_batch_config *cfg, void *stream,
+                     lbm_batch **out) {
+  if (!out || n < 1 || !inst) return LBM_EINVAL;
+  *out = nullptr;
+  lbm_batch *B = new (std::nothrow) lbm_batch();
+  if (!B) return LBM_ENOMEM;
+  B->n = n;
+  B->stream = (cudaStream_t)stream;
+  B->ctx.assign(n, nullptr);
+  B->hinst.resize(n);
+  B->hcur.assign(n, 0);
+  // validate the geometry and size the pool
+  size_t total = 0;
+  B->offset.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const lbm_instance_desc &d = inst[i];
+    if (d.nx < 4 || d.ny < 5 || (d.nx % 4) != 0 || d.params.precision != 32) {
+      delete B;
+      return LBM_EINVAL;
+    }
+    B->offset[i] = total;
+    total += (lbm_required_state_bytes(d.nx, d.ny, 32) + 255) & ~(size_t)255;
+  }
+  if (cudaMalloc(&B->pool, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete B;
+    return LBM_ENOMEM;
+  }
+  B->pool_bytes = total;
+  std::vector<uint8_t> mask;
+  int st = LBM_OK;
+  for (int i = 0; i < n && st == LBM_OK; ++i) {
+    const lbm_instance_desc &d = inst[i];
+    mask.assign((size_t)d.nx * d.ny, 0);
+    std::fill(mask.begin(), mask.begin() + d.nx, 1);
+    std::fill(mask.end() - d.nx, mask.end(), 1);
+    lbm_params p = d.params;
+    p.kernel = LBM_KERNEL_REFERENCE;  // the instance's own step (if ever called alone) needs no fused plan
+    st = lbm_create_with_buffer(d.nx, d.ny, &d.eos, d.T, d.tau, d.theta, mask.data(), &p, stream,
+                                (char *)B->pool + B->offset[i], lbm_required_state_bytes(d.nx, d.ny, 32), &B->ctx[i]);
+  }
+  bool ok = st == LBM_OK && cudaMalloc(&B->d_inst, (size_t)n * sizeof(BInst)) == cudaSuccess &&
+            cudaMalloc(&B->d_bar, (size_t)n * sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&B->d_abort, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&B->d_iflag, (size_t)n * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&B->d_cur, (size_t)n * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    lbm_batch_destroy(B);
+    return st != LBM_OK ? st : LBM_ENOMEM;
+  }
+  for (int i = 0; i < n; ++i) fill_inst(B->hinst[i], B->ctx[i], B->ctx[i]->d_flag);
+  if (cudaMemsetAsync(B->d_abort, 0, sizeof(int), B->stream) != cudaSuccess ||
+      cudaMemsetAsync(B->d_iflag, 0, (size_t)n * sizeof(int), B->stream) != cudaSuccess ||
+      cudaMemsetAsync(B->d_cur, 0, (size_t)n * sizeof(int), B->stream) != cudaSuccess) {
+    cudaGetLastError();
+    lbm_batch_destroy(B);
+    return LBM_ECUDA;
+  }
+  lbm_batch_config c;
+  lbm_batch_config_default(&c);
+  if (cfg) c = *cfg;
+  if ((st = resolve_config(B, &c, &B->cfg)) != LBM_OK || (st = plan(B)) != LBM_OK) {
+    lbm_batch_destroy(B);
+    return st;
+  }
+  *out = B;
+  return LBM_OK;
+}
+
+int lbm_batch_size(const lbm_batch *B) { return B ? B->n : 0; }
+
+lbm_ctx *lbm_batch_instance(lbm_batch *B, int i) {
+  if (!B || i < 0 || i >= B->n) return nullptr;
+  return B->ctx[i];
+}
+
+int lbm_batch_get_config(const lbm_batch *B, lbm_batch_config *cfg) {
+  if (!B || !cfg) return LBM_EINVAL;
+  *cfg = B->cfg;
+  return LBM_OK;
+}
+
+int lbm_batch_set_config(lbm_batch *B, const lbm_batch_config *cfg) {
+  if (!B || !cfg) return LBM_EINVAL;
+  lbm_batch_config c;
+  int st = resolve_config(B, cfg, &c);
+  if (st) return st;
+  const lbm_batch_config old = B->cfg;
+  B->cfg = c;
+  if ((st = plan(B)) != LBM_OK) {
+    B->cfg = old;
+    plan(B);
+    return st;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *B, int nsteps) {
+  if (!B || nsteps < 0) return LBM_EINVAL;
+  if (B->status) return B->status;
+  if (nsteps == 0) return LBM_OK;
+  int st = sync_cur(B);
+  if (st) return st;
+  if ((st = run_steps(B, nsteps)) != LBM_OK) {
+    B->status = st;
+    return st;
+  }
+  B->phase = (B->phase + nsteps) & 1;
+  B->steps += nsteps;
+  for (int i = 0; i < B->n; ++i) {
+    B->ctx[i]->cur ^= nsteps & 1;
+    B->ctx[i]->steps += nsteps;
+  }
+  return read_batch_flags(B);
+}
+
+int lbm_batch_status(lbm_batch *B, int *inst_status) {
+  if (!B) return LBM_EINVAL;
+  int st = read_batch_flags(B);
+  if (inst_status)
+    for (int i = 0; i < B->n; ++i) inst_status[i] = B->ctx[i]->status;
+  return st;
+}
+
+int lbm_batch_contact_angles(lbm_batch *B, int wall, double *theta, double *H, double *L, int *status) {
+  if (!B || (wall != 0 && wall != 1) || !theta) return LBM_EINVAL;
+  for (int i = 0; i < B->n; ++i) {
+    double t = NAN, h = NAN, l = NAN;
+    int st = lbm_contact_angle(B->ctx[i], wall, 0, B->ctx[i]->nx, &t, &h, &l);
+    if (st == LBM_ECUDA) return st;
+    theta[i] = t;
+    if (H) H[i] = h;
+    if (L) L[i] = l;
+    if (status) status[i] = st;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch *B, int trial_steps, lbm_batch_config *best) {
+  if (!B || trial_steps < 2) return LBM_EINVAL;
+  if (B->status) return B->status;
+  trial_steps += trial_steps & 1;  // every trial ends on the parity it started from
+  int st = sync_cur(B);
+  if (st) return st;
+  // the trials run on a copy of the state; the original is put back afterwards
+  void *save = nullptr;
+  if (cudaMalloc(&save, B->pool_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  std::vector<int> cur0(B->n);
+  for (int i = 0; i < B->n; ++i) cur0[i] = B->ctx[i]->cur;
+  const int phase0 = B->phase;
+  cudaError_t e = cudaMemcpyAsync(save, B->pool, B->pool_bytes, cudaMemcpyDeviceToDevice, B->stream);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  const lbm_batch_config start = B->cfg;
+  lbm_batch_config cur = start;
+  cur.graph_launches = 0;
+  cur.hold_instance = -1;
+  double best_ms = INFINITY;
+  lbm_batch_config best_cfg = cur;
+  auto trial = [&](const lbm_batch_config &c) -> int {
+    lbm_batch_config r;
+    if (resolve_config(B, &c, &r) != LBM_OK) return LBM_OK;  // not applicable to this batch
+    B->cfg = r;
+    int s = plan(B);
+    if (s == LBM_EUNSUPPORTED) return LBM_OK;
+    if (s) return s;
+    s = run_steps(B, 2);  // warm-up
+    if (s) return s;
+    BCK(cudaEventRecord(t0, B->stream));
+    s = run_steps(B, trial_steps);
+    if (s) return s;
+    BCK(cudaEventRecord(t1, B->stream));
+    BCK(cudaEventSynchronize(t1));
+    float ms = 0;
+    BCK(cudaEventElapsedTime(&ms, t0, t1));
+    int ab = 0;
+    BCK(cudaMemcpy(&ab, B->d_abort, sizeof(int), cudaMemcpyDeviceToHost));
+    if (ab) return LBM_ETIMEOUT;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_cfg = r;
+    }
+    return LBM_OK;
+  };
+  if (e == cudaSuccess) {
+    const int threads[2] = {128, 256};
+    const int stages[3] = {3, 4, 5};
+    const int bands[5] = {8, 16, 32, 64, 128};
+    const int kk[3] = {1, 8, 32};
+    // coordinate descent: threads x stages, then the band height per size class, then steps per launch
+    for (int a = 0; a < 2 && st == LBM_OK; ++a)
+      for (int b = 0; b < 3 && st == LBM_OK; ++b) {
+        lbm_batch_config c = cur;
+        c.threads = threads[a];
+        c.stages = stages[b];
+        st = trial(c);
+      }
+    cur = best_cfg;
+    for (int cls = 0; cls < 4 && st == LBM_OK; ++cls) {
+      bool present = false;
+      for (int i = 0; i < B->n; ++i) present |= size_class(B->ctx[i]->nx) == cls;
+      if (!present) continue;
+      for (int b = 0; b < 5 && st == LBM_OK; ++b) {
+        lbm_batch_config c = cur;
+        c.band_rows[cls] = bands[b];
+        st = trial(c);
+      }
+      cur = best_cfg;
+    }
+    for (int b = 0; b < 3 && st == LBM_OK; ++b) {
+      lbm_batch_config c = cur;
+      c.steps_per_launch = kk[b];
+      st = trial(c);
+    }
+    cur = best_cfg;
+  } else {
+    cudaGetLastError();
+    st = LBM_ECUDA;
+  }
+  // restore the state and install the winner (with the caller's graph and wait settings)
+  if (st == LBM_OK) {
+    cur.graph_launches = start.graph_launches;
+    cur.wait_seconds = start.wait_seconds;
+    cur.hold_instance = start.hold_instance;
+    B->cfg = cur;
+    st = plan(B);
+  } else {
+    B->cfg = start;
+    plan(B);
+  }
+  if (cudaMemcpyAsync(B->pool, save, B->pool_bytes, cudaMemcpyDeviceToDevice, B->stream) != cudaSuccess ||
+      cudaMemsetAsync(B->d_iflag, 0, (size_t)B->n * sizeof(int), B->stream) != cudaSuccess ||
+      cudaStreamSynchronize(B->stream) != cudaSuccess) {
+    cudaGetLastError();
+    st = LBM_ECUDA;
+  }
+  for (int i = 0; i < B->n; ++i) {
+    B->ctx[i]->cur = cur0[i];
+    int z[2] = {0, 0};
+    if (cudaMemcpy(B->ctx[i]->d_flag, z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) st = LBM_ECUDA;
+    B->ctx[i]->status = 0;
+  }
+  B->phase = phase0 ^ 1;  // forces a re-upload of the per-instance array indices
+  sync_cur(B);
+  cudaFree(save);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (st == LBM_OK && best) *best = B->cfg;
+  return st;
+}
+
+unsigned long long lbm_batch_launch_count(const lbm_batch *B) { return B ? B->launches : 0ULL; }
+
+int lbm_batch_get_plan(const lbm_batch *B, int *grid, int *items, int *smem_bytes, int *ctas_per_sm) {
+  if (!B) return LBM_EINVAL;
+  if (grid) *grid = B->grid;
+  if (items) *items = (int)B->items.size();
+  if (smem_bytes) *smem_bytes = B->smem;
+  if (ctas_per_sm) *ctas_per_sm = B->occ;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  else cudaDeviceSynchronize();
+  drop_graphs(B);
+  for (lbm_ctx *C : B->ctx)
+    if (C) lbm_destroy(C);
+  cudaFree(B->pool);
+  cudaFree(B->d_inst);
+  cudaFree(B->d_items);
+  cudaFree(B->d_cta_first);
+  cudaFree(B->d_bar);
+  cudaFree(B->d_abort);
+  cudaFree(B->d_iflag);
+  cudaFree(B->d_cur);
+  cudaGetLastError();
+  delete B;
+}
+
+}  // extern "C"

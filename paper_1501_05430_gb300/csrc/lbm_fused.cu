@@ -29,8 +29,14 @@
 #include <stdlib.h>
 
 #include "lbm_internal.h"
+#include "lbm_node.cuh"
 
 namespace {
+
+using lbm_node::collide_node;
+using lbm_node::eos_node;
+using lbm_node::ghost_node;
+using lbm_node::sqrt0;
 
 constexpr int NCONS = 128;               // threads per CTA (4 warps)
 constexpr int HB = 4;                    // halo box width (16 bytes of floats)
@@ -134,144 +140,6 @@ struct Seq {
   }
   __device__ bool solid(const FusedArgs &P) const { return P.walls && (v == 0 || v == P.ny - 1); }
 };
-
-// sqrt for x >= 0 through the hardware reciprocal square root; exactly 0 at 0.
-__device__ __forceinline__ float sqrt0(float x) { return x * rsqrtf(fmaxf(x, 1.17549435e-38f)); }
-
-// Window entry of one node: rho, psi and psi^2 = -2U (Eq. 10 with G = -1 and
-// the Carnahan-Starling or Eq. 11 EOS; psi = 0 where U >= 0).  U itself is
-// recovered as -psi^2/2 wherever the force needs it.
-__device__ __forceinline__ float4 eos_node(const FusedArgs &P, float rho) {
-  float m2u;  // -2U = 2 (rho/3 - p)
-  if (P.kind == LBM_EOS_CARNAHAN_STARLING) {
-    float e = P.b4 * rho;
-    float om = 1.0f - e;
-    float num = fmaf(e, fmaf(e, 1.0f - e, 1.0f), 1.0f);
-    float p = rho * P.RT * __fdividef(num, om * om * om) - P.a * rho * rho;
-    m2u = fmaf(rho, 2.0f / 3.0f, -2.0f * p);
-  } else {
-    // Eq. 11 written branch-free: p = rho th_v + (th_m - th_v)(rho - rho1)^+ + (th_l - th_m)(rho - rho2)^+
-    m2u = fmaf(P.pc2, fmaxf(rho - P.r2, 0.0f), fmaf(P.pc1, fmaxf(rho - P.r1, 0.0f), P.pc0 * rho));
-  }
-  float psi2 = fmaxf(0.0f, m2u);
-  return make_float4(rho, sqrt0(psi2), psi2, 0.0f);
-}
-
-// Eqs. 19-21 ghost entry from the boundary-row (r1) and second-row (r2)
-// densities of the window at column c; coefficient index gx; top: 0 or 1.
-__device__ __forceinline__ float4 ghost_node(const FusedArgs &P, const float *r1, const float *r2, int c, int gx,
-                                             int top) {
-  float cc = (float)P.coef[top * P.nx + gx], cot = (float)P.coef[(2 + top) * P.nx + gx];
-  float rl = r1[c + 1], rr = r1[c + 3], ri1 = r1[c + 2], ri2 = r2[c + 2];
-  float aa = rr - rl, g;
-  if (P.n_iter <= 0) {
-    g = fmaf(cot, fabsf(aa), ri2);
-  } else {
-    float d = 2.0f * (ri2 - ri1);
-    g = ri2;
-    for (int k = 0; k < P.n_iter; ++k) {
-      g = fmaf(cc, sqrt0(fmaf(aa, aa, d * d)), ri2);
-      d = ri2 - g;
-    }
-  }
-  g = fminf(fmaxf(g, 0.0f), P.ghost_max);
-  return g < P.rho_max ? eos_node(P, g) : make_float4(g, 0.0f, 0.0f, 0.0f);  // psi = U = 0 at rho_max
-}
-
-// Force (Eq. 9, + Eq. 14), Eq. 17 tensor, MRT collision with the Eq. 6
-// forcing and the Eq. 16 source for one node.  nb[0..8]: (psi, psi^2) at
-// x+e_0..x+e_8; rho: its density; f[9]: its populations; returns f*.  UNIT: every
-// non-conserved rate equals 1 (the relaxation matrix diag(0,1,...,1) of
-// Sec. 3.1), so m* = m_eq + S/2 + C needs only rho and j from f.
-template <bool UNIT>
-__device__ __forceinline__ void collide_node(const FusedArgs &P, const float *f, const float2 *nb, float rho, int y,
-                                             float *fs) {
-  const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
-  const float p0 = nb[0].x;
-  // Eq. 9 (G = -1, U = -psi^2/2) and Eq. 17 (with its G/2 prefactor) weigh
-  // the neighbours' psi and psi^2 with the same two coefficients, so both act
-  // on one combined value per neighbour:
-  //   g_a = (1 - A) psi_0 psi_a + (A/2) psi_a^2
-  //   F   = sum_a w_a g_a e_a,    Q = (-kappa/2) sum_a w_a (g_a - g_0) e_a e_a
-  const float c1 = P.omA * p0;
-  float g[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) g[k] = fmaf(c1, nb[k].x, P.halfA * nb[k].y);
-  const float gd57 = g[5] - g[7], gd86 = g[8] - g[6];
-  float Fx = fmaf(w1, g[1] - g[3], w2 * (gd57 + gd86));
-  float Fy = fmaf(w1, g[2] - g[4], w2 * (gd57 - gd86));
-  if (P.wetting == LBM_WET_MARTYS_CHEN && P.walls) {
-    // Eq. 14 for flat solid rows: sum_a w_a S e_a = (0, -1/2) below, (0, 1/2) above
-    float ssy = (y == 1 ? -0.5f : 0.0f) + (y == P.ny - 2 ? 0.5f : 0.0f);
-    Fy = fmaf(-P.Gw * p0, ssy, Fy);
-  }
-  const float gs57 = g[5] + g[7], gs68 = g[6] + g[8];
-  const float gq = w2 * fmaf(-4.0f, g[0], gs57 + gs68);
-  const float Qxx = P.pre * fmaf(w1, fmaf(-2.0f, g[0], g[1] + g[3]), gq);
-  const float Qyy = P.pre * fmaf(w1, fmaf(-2.0f, g[0], g[2] + g[4]), gq);
-  const float Qxy = P.pre * (w2 * (gs57 - gs68));
-  // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy)
-  const float s13 = f[1] - f[3], s24 = f[2] - f[4];
-  const float d57 = f[5] - f[7], d86 = f[8] - f[6];
-  const float jx = s13 + (d57 + d86);
-  const float jy = s24 + (d57 - d86);
-  // velocity with the half-force shift
-  const float ir = __fdividef(1.0f, rho);
-  const float vx = fmaf(0.5f, Fx, jx) * ir, vy = fmaf(0.5f, Fy, jy) * ir;
-  const float rvx = rho * vx, rvy = rho * vy;
-  const float v2 = fmaf(vx, vx, vy * vy);
-  const float vF = fmaf(vx, Fx, vy * Fy);
-  const float sQ = Qxx + Qyy, dQ = Qxx - Qyy;
-  float es, epss, qxs, qys, pxxs, pxys;
-  if (UNIT) {
-    // m* = m_eq + S/2 + C with s = 1
-    es = fmaf(rho, fmaf(3.0f, v2, -2.0f), fmaf(3.0f, vF, 1.5f * sQ));
-    epss = fmaf(rho, fmaf(-3.0f, v2, 1.0f), -3.0f * vF);
-    qxs = fmaf(-0.5f, Fx, -rvx);
-    qys = fmaf(-0.5f, Fy, -rvy);
-    pxxs = fmaf(rvx, vx, fmaf(-rvy, vy, fmaf(vx, Fx, fmaf(-vy, Fy, -dQ))));
-    pxys = fmaf(rvx, vy, fmaf(0.5f, fmaf(vx, Fy, vy * Fx), -Qxy));
-  } else {
-    const float a13 = f[1] + f[3], a24 = f[2] + f[4];
-    const float ax = a13 + a24, dg = (f[5] + f[6]) + (f[7] + f[8]);
-    const float me = fmaf(-4.0f, f[0], fmaf(2.0f, dg, -ax));
-    const float meps = fmaf(4.0f, f[0], fmaf(-2.0f, ax, dg));
-    const float mqx = fmaf(-2.0f, s13, d57 + d86);
-    const float mqy = fmaf(-2.0f, s24, d57 - d86);
-    const float mpxx = a13 - a24;
-    const float mpxy = (f[5] + f[7]) - (f[6] + f[8]);
-    // relaxation (Eq. 15) with forcing S (Eq. 6) and source C (Eq. 16)
-    es = fmaf(-P.se, fmaf(-rho, fmaf(3.0f, v2, -2.0f), me), me) + fmaf(P.he * 6.0f, vF, 1.5f * P.se * sQ);
-    epss = fmaf(-P.seps, fmaf(-rho, fmaf(-3.0f, v2, 1.0f), meps), meps) - P.heps * 6.0f * vF;
-    qxs = fmaf(-P.sq, mqx + rvx, mqx) - P.hq * Fx;
-    qys = fmaf(-P.sq, mqy + rvy, mqy) - P.hq * Fy;
-    pxxs = fmaf(-P.snu, fmaf(-rvx, vx, fmaf(rvy, vy, mpxx)), mpxx) +
-           fmaf(P.hnu * 2.0f, fmaf(vx, Fx, -vy * Fy), -P.snu * dQ);
-    pxys = fmaf(-P.snu, fmaf(-rvx, vy, mpxy), mpxy) + fmaf(P.hnu, fmaf(vx, Fy, vy * Fx), -P.snu * Qxy);
-  }
-  const float jxs = jx + Fx, jys = jy + Fy;
-  // back to populations: f* = M^T diag(1/N) m*.  rho/9 is rounded through one
-  // correction step: a plain product with a rounded 1/9 biases the mass.
-  const float c9 = 1.0f / 9.0f;
-  float r0 = rho * c9;
-  r0 = fmaf(fmaf(-9.0f, r0, rho), c9, r0);
-  float r1 = es * (1.0f / 36.0f), r2 = epss * (1.0f / 36.0f);
-  float r3 = jxs * (1.0f / 6.0f), r4 = qxs * (1.0f / 12.0f), r5 = jys * (1.0f / 6.0f), r6 = qys * (1.0f / 12.0f);
-  float r7 = pxxs * 0.25f, r8 = pxys * 0.25f;
-  fs[0] = fmaf(4.0f, r2 - r1, r0);
-  float Aax = fmaf(-2.0f, r2, r0 - r1);
-  float Bdg = fmaf(2.0f, r1, r0 + r2);
-  float X1 = fmaf(-2.0f, r4, r3), Y1 = fmaf(-2.0f, r6, r5);
-  fs[1] = (Aax + X1) + r7;
-  fs[3] = (Aax - X1) + r7;
-  fs[2] = (Aax + Y1) - r7;
-  fs[4] = (Aax - Y1) - r7;
-  float X2 = r3 + r4, Y2 = r5 + r6;
-  fs[5] = (Bdg + X2) + (Y2 + r8);
-  fs[6] = (Bdg - X2) + (Y2 - r8);
-  fs[7] = (Bdg - X2) - (Y2 - r8);
-  fs[8] = (Bdg + X2) - (Y2 + r8);
-}
 
 template <bool UNIT, int NC>
 __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)

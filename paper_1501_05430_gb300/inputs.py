@@ -178,9 +178,12 @@ def throughput(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: int =
                     notes=f"radius scale factors per wall {scales[0]:.4f}, {scales[1]:.4f}")
 
 
-def batched(seed: int = 42, count: int = 256):
-    """Independent instances: size uniform over four classes, theta ~ U(20, 160) deg,
-    T/Tc in {0.5, 0.6, 0.7, 0.8}, tau ~ U[0.6, 1.0], R0 = nx/4."""
+def batched(seed: int = 42, count: int = 256, width: float = 3.0):
+    """Independent droplet instances: size uniform over {128x64, 256x128,
+    384x192, 512x256}, theta ~ U(20, 160) deg, T/Tc in {0.5, 0.6, 0.7, 0.8},
+    tau ~ U[0.6, 1.0], R0 = nx/4 centred on the bottom wall.  Carnahan-Starling
+    with a = 0.25 (the coexistence densities depend only on b and T/Tc) and the
+    low-temperature MRT rates below T/Tc = 0.7, as for single_droplet."""
     rng = np.random.default_rng(seed)
     sizes = [(128, 64), (256, 128), (384, 192), (512, 256)]
     out = []
@@ -191,5 +194,5 @@ def batched(seed: int = 42, count: int = 256):
         tau = rng.uniform(0.6, 1.0)
         out.append(Workload(f"batch{i}_{nx}x{ny}", nx, ny, tr, tau, 10000, [(nx / 2.0, nx / 4.0, 0)],
                             theta_field(nx, ny, np.deg2rad(th)), [(0, 0, nx)], [th],
-                            dict(LOW_T_RATES) if tr < 0.7 else {}))
+                            dict(LOW_T_RATES) if tr < 0.7 else {}, width=width, eos=cs_eos(a=0.25)))
     return out

@@ -64,6 +64,17 @@ class lbm_info(ctypes.Structure):
                 ("tile_stages", c_int), ("steps_done", ctypes.c_longlong)]
 
 
+class lbm_instance_desc(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("eos", lbm_eos), ("T", c_double), ("tau", c_double),
+                ("theta", DP), ("params", lbm_params)]
+
+
+class lbm_batch_config(ctypes.Structure):
+    _fields_ = [("threads", c_int), ("ctas_per_sm", c_int), ("stages", c_int), ("band_rows", c_int * 4),
+                ("steps_per_launch", c_int), ("graph_launches", c_int), ("wait_seconds", c_double),
+                ("hold_instance", c_int)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -105,6 +116,21 @@ _SIGS = {
     "lbm_sync": (c_int, [c_void_p]),
     "lbm_destroy": (None, [c_void_p]),
     "lbm_mass_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "lbm_batch_config_default": (c_int, [ctypes.POINTER(lbm_batch_config)]),
+    "lbm_batch_create": (c_int, [c_int, ctypes.POINTER(lbm_instance_desc), ctypes.POINTER(lbm_batch_config),
+                                 c_void_p, ctypes.POINTER(c_void_p)]),
+    "lbm_batch_size": (c_int, [c_void_p]),
+    "lbm_batch_instance": (c_void_p, [c_void_p, c_int]),
+    "lbm_batch_step": (c_int, [c_void_p, c_int]),
+    "lbm_batch_status": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
+    "lbm_batch_contact_angles": (c_int, [c_void_p, c_int, DP, DP, DP, ctypes.POINTER(c_int)]),
+    "lbm_batch_autotune": (c_int, [c_void_p, c_int, ctypes.POINTER(lbm_batch_config)]),
+    "lbm_batch_get_config": (c_int, [c_void_p, ctypes.POINTER(lbm_batch_config)]),
+    "lbm_batch_set_config": (c_int, [c_void_p, ctypes.POINTER(lbm_batch_config)]),
+    "lbm_batch_get_plan": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                   ctypes.POINTER(c_int)]),
+    "lbm_batch_launch_count": (ctypes.c_ulonglong, [c_void_p]),
+    "lbm_batch_destroy": (None, [c_void_p]),
 }
 
 
@@ -350,6 +376,108 @@ def lbm_mass_noalloc(f_ptr, nx, ny, precision, walls, mass_ptr, stream=None):
                                    _stream_handle(stream)), "lbm_mass_noalloc")
 
 
+def lbm_batch_config_default(**overrides) -> lbm_batch_config:
+    c = lbm_batch_config()
+    _check(load().lbm_batch_config_default(ctypes.byref(c)), "lbm_batch_config_default")
+    for k, v in overrides.items():
+        if k == "band_rows":
+            for i, b in enumerate(v):
+                c.band_rows[i] = b
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def lbm_batch_create(instances, cfg=None, stream=None):
+    """instances: list of dicts with nx, ny, eos (lbm_eos), T, tau, theta
+    (radians, scalar or [ny, nx], optional) and params (lbm_params, precision
+    32).  Returns the batch handle (int)."""
+    n = len(instances)
+    descs = (lbm_instance_desc * n)()
+    keep = []
+    for i, d in enumerate(instances):
+        nx, ny = d["nx"], d["ny"]
+        descs[i].nx, descs[i].ny = nx, ny
+        descs[i].eos = d["eos"]
+        descs[i].T, descs[i].tau = d["T"], d["tau"]
+        th = d.get("theta")
+        if th is not None:
+            th = _c64(th, (ny, nx))
+            keep.append(th)
+            descs[i].theta = _dp(th)
+        descs[i].params = d.get("params") or lbm_params_default(precision=32)
+    out = c_void_p()
+    st = load().lbm_batch_create(n, descs, None if cfg is None else ctypes.byref(cfg), _stream_handle(stream),
+                                 ctypes.byref(out))
+    _check(st, "lbm_batch_create")
+    return out.value
+
+
+def lbm_batch_size(b) -> int:
+    return load().lbm_batch_size(b)
+
+
+def lbm_batch_instance(b, i):
+    ctx = load().lbm_batch_instance(b, i)
+    if not ctx:
+        raise LbmError(LBM_EINVAL, "lbm_batch_instance")
+    return ctx
+
+
+def lbm_batch_step(b, nsteps=1):
+    _check(load().lbm_batch_step(b, nsteps), "lbm_batch_step")
+
+
+def lbm_batch_status(b):
+    """(batch status, per-instance statuses as an int32 array)."""
+    n = lbm_batch_size(b)
+    out = np.zeros(n, np.int32)
+    st = load().lbm_batch_status(b, out.ctypes.data_as(ctypes.POINTER(c_int)))
+    return st, out
+
+
+def lbm_batch_contact_angles(b, wall=0):
+    """(theta, H, L, status) arrays over the instances, full width of each."""
+    n = lbm_batch_size(b)
+    th, H, L = np.zeros(n), np.zeros(n), np.zeros(n)
+    stv = np.zeros(n, np.int32)
+    _check(load().lbm_batch_contact_angles(b, wall, _dp(th), _dp(H), _dp(L),
+                                           stv.ctypes.data_as(ctypes.POINTER(c_int))), "lbm_batch_contact_angles")
+    return th, H, L, stv
+
+
+def lbm_batch_autotune(b, trial_steps=20) -> lbm_batch_config:
+    c = lbm_batch_config()
+    _check(load().lbm_batch_autotune(b, trial_steps, ctypes.byref(c)), "lbm_batch_autotune")
+    return c
+
+
+def lbm_batch_get_config(b) -> lbm_batch_config:
+    c = lbm_batch_config()
+    _check(load().lbm_batch_get_config(b, ctypes.byref(c)), "lbm_batch_get_config")
+    return c
+
+
+def lbm_batch_set_config(b, cfg: lbm_batch_config):
+    _check(load().lbm_batch_set_config(b, ctypes.byref(cfg)), "lbm_batch_set_config")
+
+
+def lbm_batch_get_plan(b):
+    """dict(grid, items, smem_bytes, ctas_per_sm) of the current launch shape."""
+    v = [c_int() for _ in range(4)]
+    _check(load().lbm_batch_get_plan(b, *[ctypes.byref(x) for x in v]), "lbm_batch_get_plan")
+    return dict(zip(("grid", "items", "smem_bytes", "ctas_per_sm"), (x.value for x in v)))
+
+
+def lbm_batch_launch_count(b) -> int:
+    return load().lbm_batch_launch_count(b)
+
+
+def lbm_batch_destroy(b):
+    if b:
+        load().lbm_batch_destroy(b)
+
+
 # ---- convenience wrapper ------------------------------------------------------
 
 class Lbm:
@@ -441,3 +569,74 @@ class Lbm:
 
     def sync(self):
         lbm_sync(self.ctx)
+
+
+class _Instance(Lbm):
+    """A context owned by a batch (lbm_batch_instance): every Lbm method works
+    on it; closing it does nothing."""
+
+    def __init__(self, ctx, nx, ny, stream):
+        self.nx, self.ny, self.stream, self._state, self.ctx = nx, ny, stream, None, ctx
+
+    def close(self):
+        self.ctx = None
+
+
+class LbmBatch:
+    """Many instances advanced by the batched persistent kernel (lbm_batch_*).
+    ``instances`` as for lbm_batch_create; ``cfg`` an lbm_batch_config or None;
+    ``stream`` a torch.cuda.Stream, a raw handle, or None."""
+
+    def __init__(self, instances, cfg=None, stream=None):
+        self.stream = stream
+        self.b = lbm_batch_create(instances, cfg, stream)
+        self.instances = [_Instance(lbm_batch_instance(self.b, i), d["nx"], d["ny"], stream)
+                          for i, d in enumerate(instances)]
+
+    def __len__(self):
+        return len(self.instances)
+
+    def __getitem__(self, i):
+        return self.instances[i]
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+
+    def status(self):
+        return lbm_batch_status(self.b)
+
+    def contact_angles(self, wall=0):
+        return lbm_batch_contact_angles(self.b, wall)
+
+    def autotune(self, trial_steps=20):
+        return lbm_batch_autotune(self.b, trial_steps)
+
+    config = property(lambda self: lbm_batch_get_config(self.b))
+
+    def set_config(self, cfg):
+        lbm_batch_set_config(self.b, cfg)
+
+    def plan(self):
+        return lbm_batch_get_plan(self.b)
+
+    def launches(self):
+        return lbm_batch_launch_count(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            for inst in self.instances:
+                inst.close()
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

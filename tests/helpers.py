@@ -25,13 +25,15 @@ def resolve_rates(tau, rates=None):
     return r
 
 
-class Pair:
-    """An oracle Sim and a GPU context with identical inputs."""
+class Case:
+    """The inputs of one simulation on both sides: the oracle Sim and the
+    liblbm parameters (lbm_params, EOS, T, tau, theta) built from the same
+    numbers."""
 
     def __init__(self, nx, ny, *, t_over_tc=0.8, tau=1.0, eos="cs", pw=None, theta=np.pi / 2, walls=True,
                  A=-0.6, kappa=0.5, G_w=0.0, n_iter=4, wetting=0, rates=None, precision=64,
-                 kernel=L.LBM_KERNEL_AUTO, check_every=0, torch_state=False, stream=None):
-        self.nx, self.ny = nx, ny
+                 kernel=L.LBM_KERNEL_AUTO, check_every=0):
+        self.nx, self.ny, self.tau, self.walls = nx, ny, tau, walls
         if eos == "pw":
             eos = dict(kind="pw", theta_v=pw[0], theta_m=pw[1], theta_l=pw[2], rho1=pw[3], rho2=pw[4])
         elif eos == "cs":
@@ -50,16 +52,34 @@ class Pair:
         self.rho_max = O.rho_max(self.oeos, self.T, self.rho_l)
         self.rho_mid = 0.5 * (self.rho_v + self.rho_l)
         r = resolve_rates(tau, rates)
-        theta = np.broadcast_to(np.asarray(theta, dtype=float), (ny, nx)).copy()
-        self.theta = theta
+        self.theta = np.broadcast_to(np.asarray(theta, dtype=float), (ny, nx)).copy()
         self.orc = O.Sim(nx, ny, self.oeos, self.T, tau=tau, walls=walls, A=A, kappa=kappa, G_w=G_w,
-                         n_iter=n_iter, wetting=wetting, theta=theta, rates=r, rho_max_=self.rho_max)
-        p = L.lbm_params_default(A=A, kappa=kappa, G_w=G_w, n_iter=n_iter, wetting=wetting, precision=precision,
-                                 kernel=kernel, s_e=r["s_e"], s_eps=r["s_eps"], s_j=r["s_j"], s_q=r["s_q"],
-                                 s_nu=r["s_nu"], check_every=check_every, rho_max=min(self.rho_max, 1e300),
-                                 rho_mid=self.rho_mid)
-        self.gpu = L.Lbm(nx, ny, self.geos, self.T, tau, theta=theta, walls=walls, params=p, stream=stream,
-                         torch_state=torch_state)
+                         n_iter=n_iter, wetting=wetting, theta=self.theta, rates=r, rho_max_=self.rho_max)
+        self.params = L.lbm_params_default(A=A, kappa=kappa, G_w=G_w, n_iter=n_iter, wetting=wetting,
+                                           precision=precision, kernel=kernel, s_e=r["s_e"], s_eps=r["s_eps"],
+                                           s_j=r["s_j"], s_q=r["s_q"], s_nu=r["s_nu"], check_every=check_every,
+                                           rho_max=min(self.rho_max, 1e300), rho_mid=self.rho_mid)
+
+    def desc(self):
+        """Instance description for lbm_batch_create (FP32)."""
+        p = L.lbm_params()
+        ctypes_copy(p, self.params)
+        p.precision = 32
+        return dict(nx=self.nx, ny=self.ny, eos=self.geos, T=self.T, tau=self.tau, theta=self.theta, params=p)
+
+
+def ctypes_copy(dst, src):
+    for name, _ in src._fields_:
+        setattr(dst, name, getattr(src, name))
+
+
+class Pair(Case):
+    """An oracle Sim and a GPU context with identical inputs."""
+
+    def __init__(self, nx, ny, *, torch_state=False, stream=None, **kw):
+        super().__init__(nx, ny, **kw)
+        self.gpu = L.Lbm(nx, ny, self.geos, self.T, self.tau, theta=self.theta, walls=self.walls,
+                         params=self.params, stream=stream, torch_state=torch_state)
 
     def set_rho(self, rho):
         self.orc.set_rho(rho)
