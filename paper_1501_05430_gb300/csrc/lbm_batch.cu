@@ -3,14 +3,18 @@
 //
 // Work list: every instance is cut into "items", bands of whole fluid rows
 // (full width, so the periodic x neighbours are in the CTA's own window).  The
-// items of all instances form one list, ordered by instance and row; the host
-// splits it into one contiguous, cost-balanced range per CTA.  A launch runs
-// `steps` timesteps.  Between two steps of the same instance the CTAs that own
-// its items meet at a per-instance barrier: a global arrival counter, released
-// with a fence + atomic add, acquired with a bounded spin on %globaltimer.  A
-// wait that runs out sets a per-instance timeout bit and a batch abort word,
-// and every CTA leaves at its next item.  Instances never wait on each other,
-// so a small instance owned by one CTA never synchronises beyond its CTA.
+// items of all instances form one list, ordered by instance and row.  A launch
+// runs `steps` timesteps as the sequence (step, item) = (0, 0), (0, 1), ...,
+// (1, 0), ...; every CTA of the persistent grid takes the next entry from a
+// global counter, so the work balances itself and steps overlap across
+// instances.  Before an item of step s the CTA waits until every item of the
+// same instance has finished step s-1: a per-instance arrival counter,
+// released with a fence + atomic add, acquired with a bounded spin on
+// %globaltimer.  Entries are taken in order and every CTA is resident
+// (cooperative launch), so the entries a wait depends on are always finished or
+// in progress.  A wait that runs out sets a per-instance timeout bit and a
+// batch abort word, and every CTA leaves at its next entry.  Instances never
+// wait on each other.
 //
 // Rows are streamed through a ring of shared-memory stages with 16-byte
 // cp.async copies that bypass L1 (.cg), so rows written by other CTAs in the
@@ -62,8 +66,9 @@ struct BItem {
 struct BatchArgs {
   const BInst *inst;
   const BItem *items;
-  const int *cta_first;    // [grid + 1]
-  unsigned *bar;           // [ninst] arrivals in this launch (zeroed before it)
+  int nitems;
+  unsigned *bar;           // [ninst] arrivals in this launch, [ninst]: next entry (zeroed before it)
+  unsigned *next;
   int *abort;              // [0]: a barrier wait ran out
   int *iflag;              // [ninst] bit 0 unstable, bit 1 timeout
   const int *cur;          // [ninst] array index holding the state at phase 0
@@ -127,14 +132,22 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
   const bool geo = P.wetting == LBM_WET_GEOMETRIC;
   const int stage_floats = 9 * nxs;
 
+  // 16-byte chunk q = tid + m NT of a row's 9 nx/4 chunks: plane a, chunk c4
+  // (the split is the same for every row, so it is advanced, not divided)
+  const int a0 = tid / nx4, c40 = tid - a0 * nx4;
   auto issue = [&](int j) {
     const int v = it.y0 - 1 + j;
     if (v <= 0 || v >= ny - 1) return;  // solid rows are not loaded
     float *st = stage + (size_t)(j % S) * stage_floats;
     const float *row = src + (size_t)v * nx;
+    int a = a0, c4 = c40;
     for (int q = tid; q < 9 * nx4; q += NT) {
-      const int a = q / nx4, c4 = q - a * nx4;
-      cp16(st + a * nxs + 4 * c4, row + a * n + 4 * c4);
+      cp16(st + a * nxs + 4 * c4, row + (unsigned)a * (unsigned)n + 4 * c4);
+      c4 += NT;
+      while (c4 >= nx4) {
+        c4 -= nx4;
+        ++a;
+      }
     }
   };
   for (int j = 0; j < S - 2; ++j) {
@@ -219,7 +232,12 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
       const float *r0w = winr + (size_t)((j - 1) & 3) * wn;
       const float *st = stage + (size_t)((j - 1) % S) * stage_floats;
       const bool wall_dn = y == 1, wall_up = y == ny - 2;
-      const size_t ry = (size_t)y * nx, rym = ry - nx, ryp = ry + nx;
+      // warp-uniform plane pointers; each store adds one 32-bit element offset
+      // (9 nx ny < 2^31 is checked at creation)
+      const unsigned un = (unsigned)n;
+      float *const o0 = dst, *const o1 = o0 + un, *const o2 = o1 + un, *const o3 = o2 + un, *const o4 = o3 + un;
+      float *const o5 = o4 + un, *const o6 = o5 + un, *const o7 = o6 + un, *const o8 = o7 + un;
+      const unsigned ry = (unsigned)y * nx, rym = ry - nx, ryp = ry + nx;
 #pragma unroll
       for (int k = 0; k < kMaxCpt; ++k) {
         const int c = tid + k * NT;
@@ -239,28 +257,28 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
 #pragma unroll
         for (int a = 0; a < 9; ++a) f[a] = st[a * nxs + c];
         collide_node<UNIT>(P, f, nb, r0w[i0], y, fs);
-        const int x = c;
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-        dst[ry + x] = fs[0];
-        dst[n + ry + xp] = fs[1];
-        dst[3 * n + ry + xm] = fs[3];
+        const unsigned x = c;
+        const unsigned xm = c == 0 ? nx - 1 : c - 1, xp = c == nx - 1 ? 0 : c + 1;
+        o0[ry + x] = fs[0];
+        o1[ry + xp] = fs[1];
+        o3[ry + xm] = fs[3];
         if (wall_up) {
-          dst[4 * n + ry + x] = fs[2];
-          dst[7 * n + ry + x] = fs[5];
-          dst[8 * n + ry + x] = fs[6];
+          o4[ry + x] = fs[2];
+          o7[ry + x] = fs[5];
+          o8[ry + x] = fs[6];
         } else {
-          dst[2 * n + ryp + x] = fs[2];
-          dst[5 * n + ryp + xp] = fs[5];
-          dst[6 * n + ryp + xm] = fs[6];
+          o2[ryp + x] = fs[2];
+          o5[ryp + xp] = fs[5];
+          o6[ryp + xm] = fs[6];
         }
         if (wall_dn) {
-          dst[2 * n + ry + x] = fs[4];
-          dst[5 * n + ry + x] = fs[7];
-          dst[6 * n + ry + x] = fs[8];
+          o2[ry + x] = fs[4];
+          o5[ry + x] = fs[7];
+          o6[ry + x] = fs[8];
         } else {
-          dst[4 * n + rym + x] = fs[4];
-          dst[7 * n + rym + xm] = fs[7];
-          dst[8 * n + rym + xp] = fs[8];
+          o4[rym + x] = fs[4];
+          o7[rym + xm] = fs[7];
+          o8[rym + xp] = fs[8];
         }
       }
     }
@@ -272,59 +290,66 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
   extern __shared__ __align__(16) float smem_f[];
   __shared__ BInst sP;
-  __shared__ int s_go, s_skip, s_bad;
+  __shared__ BItem s_it;
+  __shared__ int s_go, s_skip, s_bad, s_step, s_idx;
   const int S = A.stages, nxs = A.nxs;
   float *stage = smem_f;
   float2 *win = (float2 *)(stage + (size_t)S * 9 * nxs);
   float *winr = (float *)(win + (size_t)kSlots * (nxs + 4));
   const int tid = threadIdx.x;
-  const int i0 = A.cta_first[blockIdx.x], i1 = A.cta_first[blockIdx.x + 1];
+  const unsigned total = (unsigned)A.steps * (unsigned)A.nitems;
 
-  for (int s = 0; s < A.steps; ++s) {
-    for (int ii = i0; ii < i1; ++ii) {
-      const BItem it = A.items[ii];
-      if (tid == 0) {
-        int go = 1;
-        if (*(volatile int *)A.abort) go = 0;
+  for (;;) {
+    if (tid == 0) {
+      int go = 0;
+      const unsigned q = atomicAdd(A.next, 1u);
+      if (q < total && !*(volatile int *)A.abort) {
+        const int s = (int)(q / (unsigned)A.nitems), ii = (int)(q - (unsigned)s * (unsigned)A.nitems);
+        const BItem it = A.items[ii];
         const BInst *gp = A.inst + it.inst;
-        if (go && s > 0) {
-          // every item of the instance has finished step s-1 of this launch
-          if (!wait_ge(A.bar + it.inst, (unsigned)(s * gp->items), A.abort, A.wait_ns)) {
-            if (!*(volatile int *)A.abort) {
-              atomicOr(A.iflag + it.inst, 2);
-              atomicOr(gp->flag + 1, 1);
-            }
-            atomicExch(A.abort, 1);
-            go = 0;
+        go = 1;
+        // every item of the instance has finished step s-1 of this launch
+        if (s > 0 && !wait_ge(A.bar + it.inst, (unsigned)(s * gp->items), A.abort, A.wait_ns)) {
+          if (!*(volatile int *)A.abort) {
+            atomicOr(A.iflag + it.inst, 2);
+            atomicOr(gp->flag + 1, 1);
           }
+          atomicExch(A.abort, 1);
+          go = 0;
         }
-        s_go = go;
-        s_bad = 0;
-        // a blown-up instance is carried along (its barriers still count), not computed
-        s_skip = *(volatile const int *)(A.iflag + it.inst) & 1;
-        if (go) sP = *gp;
+        if (go) {
+          sP = *gp;
+          s_it = it;
+          s_step = s;
+          s_idx = ii;
+          // a blown-up instance is carried along (its barriers still count), not computed
+          s_skip = *(volatile const int *)(A.iflag + it.inst) & 1;
+          s_bad = 0;
+        }
       }
-      __syncthreads();
-      if (!s_go) return;
-      const int par = A.cur[it.inst] ^ ((A.phase + s) & 1);
-      bool bad = false;
-      if (!s_skip) {
-        if (sP.unit)
-          sweep<true, NT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, winr, nxs, S, bad);
-        else
-          sweep<false, NT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, winr, nxs, S, bad);
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    const BItem it = s_it;
+    const int par = A.cur[it.inst] ^ ((A.phase + s_step) & 1);
+    bool bad = false;
+    if (!s_skip) {
+      if (sP.unit)
+        sweep<true, NT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, winr, nxs, S, bad);
+      else
+        sweep<false, NT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, winr, nxs, S, bad);
+    }
+    if (bad) s_bad = 1;
+    __syncthreads();  // every store of the item issued; shared state free for the next entry
+    if (tid == 0) {
+      if (s_bad) {
+        atomicOr(A.iflag + it.inst, 1);
+        atomicOr(sP.flag, 1);
       }
-      if (bad) s_bad = 1;
-      __syncthreads();  // every store of the item issued
-      if (tid == 0) {
-        if (s_bad) {
-          atomicOr(A.iflag + it.inst, 1);
-          atomicOr(sP.flag, 1);
-        }
-        if (!(it.inst == A.hold && ii == sP.first)) {
-          __threadfence();
-          atomicAdd(A.bar + it.inst, 1u);
-        }
+      if (!(it.inst == A.hold && s_idx == sP.first)) {
+        __threadfence();
+        atomicAdd(A.bar + it.inst, 1u);
       }
     }
   }
@@ -353,17 +378,15 @@ struct lbm_batch {
   std::vector<size_t> offset; // byte offset of each instance's state in the pool
   std::vector<BInst> hinst;
   std::vector<BItem> items;
-  std::vector<int> cta_first;
   std::vector<int> hcur;      // array index of each instance's state at phase 0
   int phase;                  // steps since hcur was uploaded, mod 2
   BInst *d_inst;
   BItem *d_items;
-  int *d_cta_first;
-  unsigned *d_bar;
+  unsigned *d_bar;            // [n] arrival counters + [1] work counter
   int *d_abort;
   int *d_iflag;
   int *d_cur;
-  size_t d_items_cap, d_cta_cap;
+  size_t d_items_cap;
   int grid, nxs, smem, occ, nsm;
   cudaGraphExec_t graph[2];   // per starting phase
   int graph_steps;
@@ -418,7 +441,6 @@ int resolve_config(const lbm_batch *B, const lbm_batch_config *in, lbm_batch_con
 int plan(lbm_batch *B) {
   const lbm_batch_config &c = B->cfg;
   B->items.clear();
-  std::vector<double> cost;
   int nxmax = 0;
   for (int i = 0; i < B->n; ++i) {
     const lbm_ctx *C = B->ctx[i];
@@ -427,13 +449,13 @@ int plan(lbm_batch *B) {
     B->hinst[i].first = (int)B->items.size();
     int cnt = 0;
     for (int y = 1; y < C->ny - 1; y += band) {
-      BItem it{i, y, std::min(y + band, C->ny - 1), 0};
-      B->items.push_back(it);
-      cost.push_back((double)(it.y1 - it.y0 + 2) * C->nx);  // two halo rows per item
+      B->items.push_back(BItem{i, y, std::min(y + band, C->ny - 1), 0});
       ++cnt;
     }
     B->hinst[i].items = cnt;
   }
+  const int nitems = (int)B->items.size();
+  if ((long long)nitems * c.steps_per_launch >= (1LL << 31)) return LBM_EUNSUPPORTED;
   B->nxs = (nxmax + 3) & ~3;
   B->smem = (int)smem_bytes(B->nxs, c.stages);
   const void *kern = kernel_ptr(c.threads);
@@ -445,44 +467,15 @@ int plan(lbm_batch *B) {
   if (occ < 1) return LBM_EUNSUPPORTED;
   if (c.ctas_per_sm > 0 && c.ctas_per_sm < occ) occ = c.ctas_per_sm;
   B->occ = occ;
-  const int nitems = (int)B->items.size();
-  int grid = std::min(B->nsm * occ, nitems);
-  // contiguous ranges of about equal cost
-  double total = 0;
-  for (double w : cost) total += w;
-  B->cta_first.assign(grid + 1, nitems);
-  B->cta_first[0] = 0;
-  double acc = 0;
-  int b = 1;
-  for (int k = 0; k < nitems && b < grid; ++k) {
-    acc += cost[k];
-    while (b < grid && acc >= total * b / grid) B->cta_first[b++] = k + 1;
-  }
-  // drop CTAs left without items
-  std::vector<int> cf;
-  cf.push_back(0);
-  for (int k = 1; k <= grid; ++k)
-    if (B->cta_first[k] > cf.back()) cf.push_back(B->cta_first[k]);
-  if (cf.back() != nitems) cf.push_back(nitems);
-  B->cta_first = cf;
-  B->grid = (int)cf.size() - 1;
-  // upload
+  B->grid = std::min(B->nsm * occ, nitems);
   if ((size_t)nitems > B->d_items_cap) {
     cudaFree(B->d_items);
     B->d_items = nullptr;
     BCK(cudaMalloc(&B->d_items, (size_t)nitems * sizeof(BItem)));
     B->d_items_cap = nitems;
   }
-  if (B->cta_first.size() > B->d_cta_cap) {
-    cudaFree(B->d_cta_first);
-    B->d_cta_first = nullptr;
-    BCK(cudaMalloc(&B->d_cta_first, B->cta_first.size() * sizeof(int)));
-    B->d_cta_cap = B->cta_first.size();
-  }
   BCK(cudaMemcpyAsync(B->d_items, B->items.data(), (size_t)nitems * sizeof(BItem), cudaMemcpyHostToDevice,
                       B->stream));
-  BCK(cudaMemcpyAsync(B->d_cta_first, B->cta_first.data(), B->cta_first.size() * sizeof(int),
-                      cudaMemcpyHostToDevice, B->stream));
   BCK(cudaMemcpyAsync(B->d_inst, B->hinst.data(), (size_t)B->n * sizeof(BInst), cudaMemcpyHostToDevice, B->stream));
   BCK(cudaStreamSynchronize(B->stream));
   drop_graphs(B);
@@ -494,8 +487,9 @@ int launch(lbm_batch *B, int steps, int phase) {
   BatchArgs A;
   A.inst = B->d_inst;
   A.items = B->d_items;
-  A.cta_first = B->d_cta_first;
+  A.nitems = (int)B->items.size();
   A.bar = B->d_bar;
+  A.next = B->d_bar + B->n;
   A.abort = B->d_abort;
   A.iflag = B->d_iflag;
   A.cur = B->d_cur;
@@ -505,7 +499,7 @@ int launch(lbm_batch *B, int steps, int phase) {
   A.stages = B->cfg.stages;
   A.wait_ns = (unsigned long long)(B->cfg.wait_seconds * 1e9);
   A.hold = B->cfg.hold_instance;
-  BCK(cudaMemsetAsync(B->d_bar, 0, (size_t)B->n * sizeof(unsigned), B->stream));
+  BCK(cudaMemsetAsync(B->d_bar, 0, (size_t)(B->n + 1) * sizeof(unsigned), B->stream));
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(B->grid);
   lc.blockDim = dim3(B->cfg.threads);
@@ -678,7 +672,7 @@ int lbm_batch_create(int n, const lbm_instance_desc *inst, const lbm_batch_confi
                                 (char *)B->pool + B->offset[i], lbm_required_state_bytes(d.nx, d.ny, 32), &B->ctx[i]);
   }
   bool ok = st == LBM_OK && cudaMalloc(&B->d_inst, (size_t)n * sizeof(BInst)) == cudaSuccess &&
-            cudaMalloc(&B->d_bar, (size_t)n * sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&B->d_bar, (size_t)(n + 1) * sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc(&B->d_abort, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&B->d_iflag, (size_t)n * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&B->d_cur, (size_t)n * sizeof(int)) == cudaSuccess;
@@ -913,7 +907,6 @@ void lbm_batch_destroy(lbm_batch *B) {
   cudaFree(B->pool);
   cudaFree(B->d_inst);
   cudaFree(B->d_items);
-  cudaFree(B->d_cta_first);
   cudaFree(B->d_bar);
   cudaFree(B->d_abort);
   cudaFree(B->d_iflag);
