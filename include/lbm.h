@@ -283,7 +283,8 @@ int lbm_mass_noalloc(const void *f, int nx, int ny, int precision, int walls, do
  * of Secs. 3.1 and 4.2 run as one job instead of one solver per case).
  *
  * Every instance has solid rows at y = 0 and y = ny-1, precision 32, and
- * nx a multiple of 4.  Its state lives in one device pool owned by the batch.
+ * nx a multiple of 4 and at most 512.  Its state lives in one device pool
+ * owned by the batch.
  * Each instance is cut into work items (bands of whole fluid rows); one launch
  * advances every instance by steps_per_launch steps, and the CTAs that share
  * an instance meet at a per-instance barrier between its steps (no barrier
@@ -302,8 +303,8 @@ typedef struct {
 
 /* Launch shape.  Zero fields take the defaults in brackets. */
 typedef struct {
-  int threads;           /* threads per CTA, 128 or 256 [128; 256 when some nx > 512];
-                            columns per thread = ceil(nx / threads) <= 4 */
+  int threads;           /* threads per CTA, 128 or 256 [256]; each thread owns
+                            columns t, t + threads, ... of a row */
   int ctas_per_sm;       /* cap on resident CTAs per SM [occupancy maximum] */
   int stages;            /* row stages of the shared-memory copy ring, 3..6 [4] */
   int band_rows[4];      /* fluid rows per work item for nx in (0,128], (128,256],
@@ -325,7 +326,7 @@ int lbm_batch_config_default(lbm_batch_config *cfg);
  * graphs need a non-NULL stream).  Each instance starts with f = 0; set it
  * with lbm_set_rho / lbm_init_droplets / lbm_set_f on lbm_batch_instance().
  * Errors: LBM_EINVAL (n < 1, an instance's sizes, precision or parameters),
- * LBM_EUNSUPPORTED (nx > 4 * threads), LBM_ENOMEM, LBM_ECUDA. */
+ * LBM_EUNSUPPORTED (an instance wider than 512), LBM_ENOMEM, LBM_ECUDA. */
 int lbm_batch_create(int n, const lbm_instance_desc *inst, const lbm_batch_config *cfg, void *stream,
                      lbm_batch **out);
 int lbm_batch_size(const lbm_batch *b);

@@ -38,9 +38,9 @@ namespace {
 
 using lbm_node::collide_node;
 using lbm_node::eos_node;
-using lbm_node::ghost_node;
+using lbm_node::ghost_value;
 
-constexpr int kMaxCpt = 4;  // columns per thread: nx <= 4 x threads per CTA
+constexpr int kMaxNx = 512;  // widest instance: columns per thread = 512 / threads
 constexpr int kSlots = 4;   // window rows (ring)
 
 // Per-instance block: the node-function fields (same names as the fused
@@ -120,10 +120,13 @@ __device__ bool wait_ge(const unsigned *p, unsigned target, const int *abort, un
 }
 
 // One item of one step: stream virtual rows y0-1 .. y1 (halo and solid rows
-// included), fill the window, collide rows y0 .. y1-1 into dst.
-template <bool UNIT, int NT>
+// included), fill the window, collide rows y0 .. y1-1 into dst.  Thread t owns
+// columns t, t + NT, ... (CPT of them); their densities stay in registers for
+// the collision and the ghost rows, and only the boundary rows' densities (the
+// ghost rule needs their x neighbours) go to shared memory.
+template <bool UNIT, int NT, int CPT>
 __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__ src, float *__restrict__ dst,
-                      float *stage, float2 *win, float *winr, int nxs, int S, bool &bad) {
+                      float *stage, float2 *win, float *wrho, int nxs, int S, bool &bad) {
   const int tid = threadIdx.x;
   const int nx = P.nx, ny = P.ny, nx4 = nx >> 2;
   const size_t n = (size_t)nx * ny;
@@ -155,6 +158,10 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
     cp_commit();
   }
 
+  float rc[CPT], rp[CPT], rp2[CPT];  // densities of rows v, v-1, v-2 at the owned columns
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) rc[k] = rp[k] = rp2[k] = 0.0f;
+
   for (int j = 0; j < R; ++j) {
     const int v = it.y0 - 1 + j;
     cp_wait_dyn(S - 3);
@@ -163,12 +170,12 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
     cp_commit();
 
     float2 *wcur = win + (size_t)(j & 3) * wn;
-    float *rcur = winr + (size_t)(j & 3) * wn;
     const bool solid = v == 0 || v == ny - 1;
     if (!solid) {
       const float *st = stage + (size_t)(j % S) * stage_floats;
+      const bool brow = v == 1 || v == ny - 2;  // boundary row: the ghost rule reads its neighbours
 #pragma unroll
-      for (int k = 0; k < kMaxCpt; ++k) {
+      for (int k = 0; k < CPT; ++k) {
         const int c = tid + k * NT;
         if (c < nx) {
           const float *q = st + c;
@@ -177,47 +184,47 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
                           q[8 * nxs];
           const float4 e = eos_node(P, r);
           const float2 pe = make_float2(e.y, e.z);
-          rcur[c + 2] = r;
+          rc[k] = r;
           wcur[c + 2] = pe;
-          if (c == nx - 1) { rcur[1] = r; wcur[1] = pe; }
-          if (c == 0) { rcur[nx + 2] = r; wcur[nx + 2] = pe; }
+          if (c == nx - 1) wcur[1] = pe;
+          if (c == 0) wcur[nx + 2] = pe;
+          if (brow) {
+            wrho[c + 2] = r;
+            if (c == nx - 1) wrho[1] = r;
+            if (c == 0) wrho[nx + 2] = r;
+          }
           bad |= !(r > 0.0f) || r > P.rho_max;
         }
       }
-      // bottom ghost row (Eqs. 19-21) once rows 1 and 2 are in the window
+      // bottom ghost row (Eqs. 19-21) once rows 1 and 2 are in: row 1's
+      // densities in wrho (written last iteration), row 2's in registers
       if (geo && it.y0 == 1 && v == 2) {
-        const float *r1w = winr + (size_t)((j - 1) & 3) * wn;
         float2 *gw = win + (size_t)((j - 2) & 3) * wn;
-        float *gr = winr + (size_t)((j - 2) & 3) * wn;
 #pragma unroll
-        for (int k = 0; k < kMaxCpt; ++k) {
+        for (int k = 0; k < CPT; ++k) {
           const int c = tid + k * NT;
           if (c < nx) {
-            const float4 e = ghost_node(P, r1w, rcur, c, c, 0);
+            const float4 e = ghost_value(P, wrho[c + 1], wrho[c + 2], wrho[c + 3], rc[k], c, 0);
             const float2 pe = make_float2(e.y, e.z);
-            gr[c + 2] = e.x;
             gw[c + 2] = pe;
-            if (c == nx - 1) { gr[1] = e.x; gw[1] = pe; }
-            if (c == 0) { gr[nx + 2] = e.x; gw[nx + 2] = pe; }
+            if (c == nx - 1) gw[1] = pe;
+            if (c == 0) gw[nx + 2] = pe;
           }
         }
       }
     } else if (!geo || v == ny - 1) {
       // Martys-Chen: solid rows carry psi = U = 0.  Geometric: the top ghost
-      // row from rows ny-2 and ny-3 (the bottom one is filled at v == 2).
-      const float *r1w = winr + (size_t)((j - 1) & 3) * wn;
-      const float *r2w = winr + (size_t)((j - 2) & 3) * wn;
+      // row from rows ny-2 (wrho) and ny-3 (registers); the bottom one is filled at v == 2.
 #pragma unroll
-      for (int k = 0; k < kMaxCpt; ++k) {
+      for (int k = 0; k < CPT; ++k) {
         const int c = tid + k * NT;
         if (c < nx) {
           float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          if (geo) e = ghost_node(P, r1w, r2w, c, c, 1);
+          if (geo) e = ghost_value(P, wrho[c + 1], wrho[c + 2], wrho[c + 3], rp2[k], c, 1);
           const float2 pe = make_float2(e.y, e.z);
-          rcur[c + 2] = e.x;
           wcur[c + 2] = pe;
-          if (c == nx - 1) { rcur[1] = e.x; wcur[1] = pe; }
-          if (c == 0) { rcur[nx + 2] = e.x; wcur[nx + 2] = pe; }
+          if (c == nx - 1) wcur[1] = pe;
+          if (c == 0) wcur[nx + 2] = pe;
         }
       }
     }
@@ -229,7 +236,6 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
       const float2 *wm = win + (size_t)((j - 2) & 3) * wn;
       const float2 *w0 = win + (size_t)((j - 1) & 3) * wn;
       const float2 *wp = wcur;
-      const float *r0w = winr + (size_t)((j - 1) & 3) * wn;
       const float *st = stage + (size_t)((j - 1) % S) * stage_floats;
       const bool wall_dn = y == 1, wall_up = y == ny - 2;
       // warp-uniform plane pointers; each store adds one 32-bit element offset
@@ -239,7 +245,7 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
       float *const o5 = o4 + un, *const o6 = o5 + un, *const o7 = o6 + un, *const o8 = o7 + un;
       const unsigned ry = (unsigned)y * nx, rym = ry - nx, ryp = ry + nx;
 #pragma unroll
-      for (int k = 0; k < kMaxCpt; ++k) {
+      for (int k = 0; k < CPT; ++k) {
         const int c = tid + k * NT;
         if (c >= nx) break;
         const int i0 = c + 2;
@@ -256,7 +262,7 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
         float f[9], fs[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) f[a] = st[a * nxs + c];
-        collide_node<UNIT>(P, f, nb, r0w[i0], y, fs);
+        collide_node<UNIT>(P, f, nb, rp[k], y, fs);
         const unsigned x = c;
         const unsigned xm = c == 0 ? nx - 1 : c - 1, xp = c == nx - 1 ? 0 : c + 1;
         o0[ry + x] = fs[0];
@@ -282,12 +288,18 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
         }
       }
     }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      rp2[k] = rp[k];
+      rp[k] = rc[k];
+    }
   }
   cp_wait<0>();  // no copy of this item stays in flight into the next one's stages
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 5) k_batch(BatchArgs A) {
+  constexpr int CPT = kMaxNx / NT;
   extern __shared__ __align__(16) float smem_f[];
   __shared__ BInst sP;
   __shared__ BItem s_it;
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
   const int S = A.stages, nxs = A.nxs;
   float *stage = smem_f;
   float2 *win = (float2 *)(stage + (size_t)S * 9 * nxs);
-  float *winr = (float *)(win + (size_t)kSlots * (nxs + 4));
+  float *wrho = (float *)(win + (size_t)kSlots * (nxs + 4));
   const int tid = threadIdx.x;
   const unsigned total = (unsigned)A.steps * (unsigned)A.nitems;
 
@@ -336,9 +348,9 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
     bool bad = false;
     if (!s_skip) {
       if (sP.unit)
-        sweep<true, NT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, winr, nxs, S, bad);
+        sweep<true, NT, CPT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, wrho, nxs, S, bad);
       else
-        sweep<false, NT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, winr, nxs, S, bad);
+        sweep<false, NT, CPT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, wrho, nxs, S, bad);
     }
     if (bad) s_bad = 1;
     __syncthreads();  // every store of the item issued; shared state free for the next entry
@@ -358,7 +370,8 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
 const void *kernel_ptr(int nt) { return nt == 256 ? (const void *)k_batch<256> : (const void *)k_batch<128>; }
 
 size_t smem_bytes(int nxs, int stages) {
-  return (size_t)stages * 9 * nxs * sizeof(float) + (size_t)kSlots * (nxs + 4) * (sizeof(float2) + sizeof(float));
+  return (size_t)stages * 9 * nxs * sizeof(float) + (size_t)kSlots * (nxs + 4) * sizeof(float2) +
+         (size_t)(nxs + 4) * sizeof(float);
 }
 
 int size_class(int nx) { return nx <= 128 ? 0 : nx <= 256 ? 1 : nx <= 384 ? 2 : 3; }
@@ -418,9 +431,9 @@ int resolve_config(const lbm_batch *B, const lbm_batch_config *in, lbm_batch_con
   lbm_batch_config c = *in;
   int nxmax = 0;
   for (int i = 0; i < B->n; ++i) nxmax = std::max(nxmax, B->ctx[i]->nx);
-  if (c.threads == 0) c.threads = nxmax > 512 ? 256 : 128;
+  if (c.threads == 0) c.threads = 256;
   if (c.threads != 128 && c.threads != 256) return LBM_EINVAL;
-  if (nxmax > kMaxCpt * c.threads) return LBM_EUNSUPPORTED;
+  if (nxmax > kMaxNx) return LBM_EUNSUPPORTED;
   if (c.stages == 0) c.stages = 4;
   if (c.stages < 3 || c.stages > 6) return LBM_EINVAL;
   for (int k = 0; k < 4; ++k) {
@@ -459,9 +472,16 @@ int plan(lbm_batch *B) {
   B->nxs = (nxmax + 3) & ~3;
   B->smem = (int)smem_bytes(B->nxs, c.stages);
   const void *kern = kernel_ptr(c.threads);
-  BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, B->smem));
-  int dev = 0, occ = 0;
+  int dev = 0, occ = 0, optin = 0;
   BCK(cudaGetDevice(&dev));
+  // the attribute is per kernel, not per batch: allow the device maximum so
+  // that batches (and autotuner trials) with different rings coexist
+  BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  BCK(cudaFuncGetAttributes(&fa, kern));
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= the opt-in limit
+  if (B->smem > dyn_max) return LBM_EUNSUPPORTED;
+  BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
   BCK(cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, dev));
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, c.threads, B->smem));
   if (occ < 1) return LBM_EUNSUPPORTED;

@@ -476,12 +476,22 @@ int lbm_fused_plan(lbm_ctx *C) {
   const lbm_dev_params &D = C->dp;
   C->fused_unit = D.s[1] == 1.0 && D.s[2] == 1.0 && D.s[4] == 1.0 && D.s[7] == 1.0;
   const void *kern = kernel_ptr(C->fused_unit, nc);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  int dev = 0, nsm = 0, occ = 0, optin = 0;
+  cudaGetDevice(&dev);
+  // the attribute is per kernel, not per context: allow the device maximum so
+  // that contexts planned with different ring depths coexist
+  cudaFuncAttributes fa;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  int dev = 0, nsm = 0, occ = 0;
-  cudaGetDevice(&dev);
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= the opt-in limit
+  if ((int)smem > dyn_max ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NCONS, smem) != cudaSuccess || occ < 1) {
     cudaGetLastError();

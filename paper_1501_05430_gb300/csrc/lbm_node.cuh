@@ -37,13 +37,12 @@ __device__ __forceinline__ float4 eos_node(const PT &P, float rho) {
   return make_float4(rho, sqrt0(psi2), psi2, 0.0f);
 }
 
-// Eqs. 19-21 ghost entry from the boundary-row (r1) and second-row (r2)
-// densities of the window at column c; coefficient index gx; top: 0 or 1.
+// Eqs. 19-21 ghost entry at column x from the boundary-row densities rl, ri1,
+// rr (at x-1, x, x+1) and the second-row density ri2 (at x); gx indexes the
+// wall coefficients; top: 0 or 1.
 template <class PT>
-__device__ __forceinline__ float4 ghost_node(const PT &P, const float *r1, const float *r2, int c, int gx,
-                                             int top) {
+__device__ __forceinline__ float4 ghost_value(const PT &P, float rl, float ri1, float rr, float ri2, int gx, int top) {
   float cc = (float)P.coef[top * P.nx + gx], cot = (float)P.coef[(2 + top) * P.nx + gx];
-  float rl = r1[c + 1], rr = r1[c + 3], ri1 = r1[c + 2], ri2 = r2[c + 2];
   float aa = rr - rl, g;
   if (P.n_iter <= 0) {
     g = fmaf(cot, fabsf(aa), ri2);
@@ -57,6 +56,14 @@ __device__ __forceinline__ float4 ghost_node(const PT &P, const float *r1, const
   }
   g = fminf(fmaxf(g, 0.0f), P.ghost_max);
   return g < P.rho_max ? eos_node(P, g) : make_float4(g, 0.0f, 0.0f, 0.0f);  // psi = U = 0 at rho_max
+}
+
+// The same from window rows: r1 boundary row, r2 second row, column c stored
+// at index c + 2.
+template <class PT>
+__device__ __forceinline__ float4 ghost_node(const PT &P, const float *r1, const float *r2, int c, int gx,
+                                             int top) {
+  return ghost_value(P, r1[c + 1], r1[c + 2], r1[c + 3], r2[c + 2], gx, top);
 }
 
 // Force (Eq. 9, + Eq. 14), Eq. 17 tensor, MRT collision with the Eq. 6

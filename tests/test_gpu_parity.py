@@ -293,3 +293,19 @@ def test_torch_owned_state_and_stream():
     assert np.array_equal(a.gpu.f(), b.gpu.f())
     a.close()
     b.close()
+
+
+def test_contexts_with_different_fused_rings_coexist(monkeypatch):
+    """The fused kernel's launch attributes are per kernel: a context planned
+    with a deep TMA ring still launches after a shallower one is created."""
+    w = I.single_droplet(90.0)
+    monkeypatch.setenv("LBM_FUSED_STAGES", "8")
+    a = droplet_pair(w, precision=32, kernel=FUSED)
+    monkeypatch.setenv("LBM_FUSED_STAGES", "3")
+    b = droplet_pair(w, precision=32, kernel=FUSED)
+    assert a.gpu.info.tile_stages == 8 and b.gpu.info.tile_stages == 3
+    a.gpu.step(5)
+    b.gpu.step(5)
+    assert np.array_equal(a.gpu.f(), b.gpu.f())
+    a.close()
+    b.close()
