@@ -7,6 +7,11 @@ Test infrastructure only: the independent checker of the CUDA library.  Only
 gcc (``-O2 -ffp-contract=off``, no fast-math) so that its arithmetic happens in
 the written order.
 
+``autodiff.py`` restates the same step with PyTorch CPU ops in FP64 so that
+torch autograd gives the exact derivative of the oracle's step (the reference
+for the adjoint kernels); it is pinned to the C step and to its finite
+differences in ``tests/test_oracle_autodiff.py``.
+
 Parity unpinned: nothing.  Every function is pinned in ``tests/test_oracle_*``
 (see the header of each C function for what pins it).
 """
