@@ -276,6 +276,35 @@ void lbm_destroy(lbm_ctx *ctx);
 #define LBM_NOALLOC_MAX_NODES (1 << 28)
 int lbm_mass_noalloc(const void *f, int nx, int ny, int precision, int walls, double *mass, void *stream);
 
+/* ---- discrete adjoint ---------------------------------------------------- *
+ * Gradients of a function of the final density with respect to the wall
+ * angles (theta per wall node, through sin(pi/2 - theta) of Eqs. 20-21 or
+ * tan(pi/2 - theta) of Eq. 19) and the EOS temperature T, by the reverse-time
+ * (adjoint) of the step, with the initial state held fixed.  The recorded
+ * forward uses the canonical reference kernels (bit-identical to an FP64
+ * evaluation of the step in that order at precision 64), whatever kernel
+ * lbm_step uses.  Kinks: d sqrt(s)/ds = 0 at s = 0, d|a|/da = 0 at a = 0, a
+ * clamped ghost density passes no gradient.
+ *
+ * lbm_adjoint_record: advance the context by nsteps from its current state,
+ * keeping the state every checkpoint_every steps on the device (the tape:
+ * ceil(nsteps / checkpoint_every) + checkpoint_every states plus O(nx ny)
+ * scratch).  Replaces an earlier tape.  Returns LBM_OK, LBM_EUNSTABLE,
+ * LBM_EINVAL (nsteps or checkpoint_every < 1), LBM_EUNSUPPORTED
+ * (n_iter > 64), LBM_ENOMEM, LBM_ECUDA.
+ *
+ * lbm_adjoint_backward: given dL/drho at the final (recorded) time,
+ * dl_drho[ny][nx] (host, values on the solid rows ignored), walk the tape back
+ * and write dL/dtheta to dl_dtheta[2][nx] (row 0: bottom wall, row 1: top
+ * wall; zero for Martys-Chen and periodic boxes), dL/dT to *dl_dT, and
+ * dL/df at the recorded start to dl_df0[9][ny][nx]; each output may be NULL.
+ * The tape is kept, so backward may run again with another dl_drho.  The
+ * context's state is not changed.  LBM_EINVAL without a tape. */
+int lbm_adjoint_record(lbm_ctx *ctx, int nsteps, int checkpoint_every);
+int lbm_adjoint_backward(lbm_ctx *ctx, const double *dl_drho, double *dl_dtheta, double *dl_dT, double *dl_df0);
+/* Free the tape (lbm_destroy does it too). */
+int lbm_adjoint_release(lbm_ctx *ctx);
+
 /* ---- batched sweep ----------------------------------------------------- *
  * Many independent droplet instances -- each with its own grid size, EOS
  * temperature, relaxation rates and wall-angle field -- advanced together by

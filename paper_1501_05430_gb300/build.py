@@ -1,8 +1,9 @@
 """Build liblbm.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
 Translation units and their floating-point flags:
-  lbm_ref.cu, lbm_measure.cu  -fmad=false: the canonical-order kernels must not
-                               contract a*b+c into an FMA (bit-exact FP64 path)
+  lbm_ref.cu, lbm_measure.cu,  -fmad=false: the canonical-order kernels must not
+  lbm_adjoint.cu               contract a*b+c into an FMA (bit-exact FP64 path;
+                               the adjoint recomputes the same forward values)
   lbm_fused.cu, lbm_batch.cu   FMA allowed: the production FP32 step (one domain; many
                                instances in one persistent launch)
   lbm_api.cu                   host code and launch orchestration
@@ -27,8 +28,10 @@ UNITS = {
     "lbm_fused.cu": [],
     "lbm_noalloc.cu": [],
     "lbm_batch.cu": [],
+    "lbm_adjoint.cu": ["-fmad=false"],
 }
-HEADERS = [os.path.join(CSRC, "lbm_internal.h"), os.path.join(CSRC, "lbm_node.cuh"), os.path.join(ROOT, "include", "lbm.h")]
+HEADERS = [os.path.join(CSRC, h) for h in ("lbm_internal.h", "lbm_node.cuh", "lbm_ref_node.cuh")] + [
+    os.path.join(ROOT, "include", "lbm.h")]
 
 
 def _nvcc() -> str:

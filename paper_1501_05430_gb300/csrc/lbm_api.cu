@@ -333,6 +333,7 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
   C->f[1] = (char *)C->state + 9 * n * rs;
   C->red_len = 1024;
   bool ok = cudaMalloc(&C->d_coef, 4 * (size_t)nx * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&C->d_dcoef, 4 * (size_t)nx * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&C->d_flag, 2 * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&C->d_rho64, n * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&C->d_red, C->red_len * sizeof(double)) == cudaSuccess &&
@@ -344,8 +345,10 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
   }
   // Eqs. 19-21 coefficients per wall node: c = sin(pi/2 - theta) (Eqs. 20-21),
   // cot = tan(pi/2 - theta) (Eq. 19)
-  double *coef = (double *)malloc(4 * (size_t)nx * sizeof(double));
+  // and their theta derivatives for the adjoint: -cos(pi/2 - theta), -1/cos^2(pi/2 - theta)
+  double *coef = (double *)malloc(8 * (size_t)nx * sizeof(double));
   if (!coef) { lbm_destroy(C); return LBM_ENOMEM; }
+  double *dcoef = coef + 4 * (size_t)nx;
   for (int x = 0; x < nx; ++x) {
     double tb = theta ? theta[x] : M_PI / 2;
     double tt = theta ? theta[(size_t)(ny - 1) * nx + x] : M_PI / 2;
@@ -353,8 +356,15 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
     coef[nx + x] = sin(M_PI / 2 - tt);
     coef[2 * nx + x] = tan(M_PI / 2 - tb);
     coef[3 * nx + x] = tan(M_PI / 2 - tt);
+    double cb = cos(M_PI / 2 - tb), ct = cos(M_PI / 2 - tt);
+    dcoef[x] = -cb;
+    dcoef[nx + x] = -ct;
+    dcoef[2 * nx + x] = -1.0 / (cb * cb);
+    dcoef[3 * nx + x] = -1.0 / (ct * ct);
   }
   cudaError_t e1 = cudaMemcpy(C->d_coef, coef, 4 * (size_t)nx * sizeof(double), cudaMemcpyHostToDevice);
+  if (e1 == cudaSuccess)
+    e1 = cudaMemcpy(C->d_dcoef, dcoef, 4 * (size_t)nx * sizeof(double), cudaMemcpyHostToDevice);
   free(coef);
   if (e1 != cudaSuccess || cudaMemsetAsync(C->state, 0, need, C->stream) != cudaSuccess ||
       cudaMemsetAsync(C->d_flag, 0, 2 * sizeof(int), C->stream) != cudaSuccess) {
@@ -706,8 +716,10 @@ int lbm_sync(lbm_ctx *C) {
 void lbm_destroy(lbm_ctx *C) {
   if (!C) return;
   cudaStreamSynchronize(C->stream);
+  lbm_adjoint_free_tape(C);
   if (C->owns_state && C->state) cudaFree(C->state);
   if (C->d_coef) cudaFree(C->d_coef);
+  if (C->d_dcoef) cudaFree(C->d_dcoef);
   if (C->d_flag) cudaFree(C->d_flag);
   if (C->d_rho64) cudaFree(C->d_rho64);
   if (C->d_fields) cudaFree(C->d_fields);

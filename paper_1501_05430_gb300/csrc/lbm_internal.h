@@ -47,6 +47,8 @@ struct lbm_ctx {
   int status;            // sticky failure
   // device scratch
   double *d_coef;        // 4*nx: c_bot, c_top, cot_bot, cot_top
+  double *d_dcoef;       // 4*nx: their derivatives in theta (adjoint)
+  struct lbm_tape *tape; // adjoint record (lbm_adjoint.cu); NULL when none
   int *d_flag;           // [0]: instability, [1]: timeout
   double *d_rho64;       // nx*ny, measurement density
   void *d_fields;        // 3*nx*ny reals: rho, psi, U (reference kernels)
@@ -77,6 +79,9 @@ cudaError_t lbm_ref_droplets(const lbm_ctx *C, int n, const double *drop, double
 // ---- lbm_fused.cu: single-pass FP32 step ------------------------------------
 int lbm_fused_plan(lbm_ctx *C);  // sets fused_ok, tile_*, tensor maps
 cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches);
+
+// ---- lbm_adjoint.cu: discrete adjoint ---------------------------------------
+void lbm_adjoint_free_tape(lbm_ctx *C);
 
 // ---- lbm_measure.cu: reductions -------------------------------------------
 cudaError_t lbm_rho64(const lbm_ctx *C, const void *f, double *rho, unsigned long long *launches);

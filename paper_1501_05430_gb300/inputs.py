@@ -11,6 +11,7 @@ sizes of the benchmark configurations):
   single_droplet   400 x 200, CS (a = 0.25) T/Tc = 0.6, tau = 0.8, R0 = 60
   throughput       4096 x 2048, Table 1 EOS at ratio 1000, tau = 1, 12 droplets per wall
   batched          256 instances of {128x64 .. 512x256}, seeded theta, T/Tc, tau
+  adjoint_case     256 x 128, CS T/Tc = 0.7, tau = 1, R0 = 40, per-wall-node theta
 """
 from __future__ import annotations
 
@@ -196,3 +197,38 @@ def batched(seed: int = 42, count: int = 256, width: float = 3.0):
                             theta_field(nx, ny, np.deg2rad(th)), [(0, 0, nx)], [th],
                             dict(LOW_T_RATES) if tr < 0.7 else {}, width=width, eos=cs_eos(a=0.25)))
     return out
+
+
+def adjoint_case(seed: int = 7, target_seed: int = 8) -> dict:
+    """Wall-angle inversion case: 256 x 128, Carnahan-Starling (a = 1, b = 4,
+    R = 1) at T/Tc = 0.7, tau = 1, a droplet of radius 40 centred on the bottom
+    wall, 2000 steps with a checkpoint every 100.  The parameters are the 256
+    bottom-wall angles, seeded U(45, 135) deg (``theta``); the target profile
+    comes from the same run at a second seeded field (``theta_target``); the
+    top wall stays at 90 deg.  The loss is
+        L = sum_i (h_i - h*_i)^2 + (W - W*)^2,
+        h_i = sum_{y=1}^{ny-2} phi(i, y),  W = sum_i phi(i, 1),
+        phi = (rho - rho_v) / (rho_l - rho_v)
+    with rho_v, rho_l the coexistence densities at the nominal T (held fixed)."""
+    nx, ny = 256, 128
+    th = np.random.default_rng(seed).uniform(np.deg2rad(45.0), np.deg2rad(135.0), nx)
+    tt = np.random.default_rng(target_seed).uniform(np.deg2rad(45.0), np.deg2rad(135.0), nx)
+    return dict(nx=nx, ny=ny, t_over_tc=0.7, tau=1.0, eos=cs_eos(), droplet=(nx / 2.0, 40.0, 0), width=3.0,
+                theta=th, theta_target=tt, steps=2000, checkpoint_every=100)
+
+
+def profile(rho: np.ndarray, rho_v: float, rho_l: float):
+    """(h [nx], W) of a density field: h_i = sum over the fluid rows of phi,
+    W = sum over the boundary row of phi, phi = (rho - rho_v) / (rho_l - rho_v)."""
+    phi = (rho - rho_v) / (rho_l - rho_v)
+    return phi[1:-1].sum(0), float(phi[1].sum())
+
+
+def profile_loss_grad(rho: np.ndarray, h_target: np.ndarray, W_target: float, rho_v: float, rho_l: float):
+    """(L, dL/drho [ny, nx]) of the height / base-width profile loss of adjoint_case."""
+    h, W = profile(rho, rho_v, rho_l)
+    L = float(((h - h_target) ** 2).sum() + (W - W_target) ** 2)
+    g = np.zeros_like(rho)
+    g[1:-1] = 2.0 * (h - h_target)[None, :]
+    g[1] += 2.0 * (W - W_target)
+    return L, g / (rho_l - rho_v)

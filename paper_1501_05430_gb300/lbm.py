@@ -116,6 +116,9 @@ _SIGS = {
     "lbm_sync": (c_int, [c_void_p]),
     "lbm_destroy": (None, [c_void_p]),
     "lbm_mass_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "lbm_adjoint_record": (c_int, [c_void_p, c_int, c_int]),
+    "lbm_adjoint_backward": (c_int, [c_void_p, DP, DP, DP, DP]),
+    "lbm_adjoint_release": (c_int, [c_void_p]),
     "lbm_batch_config_default": (c_int, [ctypes.POINTER(lbm_batch_config)]),
     "lbm_batch_create": (c_int, [c_int, ctypes.POINTER(lbm_instance_desc), ctypes.POINTER(lbm_batch_config),
                                  c_void_p, ctypes.POINTER(c_void_p)]),
@@ -374,6 +377,27 @@ def lbm_mass_noalloc(f_ptr, nx, ny, precision, walls, mass_ptr, stream=None):
     without allocating device memory (see lbm.h).  Pointers are ints."""
     _check(load().lbm_mass_noalloc(c_void_p(f_ptr), nx, ny, precision, 1 if walls else 0, c_void_p(mass_ptr),
                                    _stream_handle(stream)), "lbm_mass_noalloc")
+
+
+def lbm_adjoint_record(ctx, nsteps, checkpoint_every=100):
+    _check(load().lbm_adjoint_record(ctx, nsteps, checkpoint_every), "lbm_adjoint_record")
+
+
+def lbm_adjoint_backward(ctx, dl_drho, want_df0=False):
+    """(dL/dtheta [2, nx], dL/dT, dL/df0 [9, ny, nx] or None) for dL/drho at the
+    recorded final time ([ny, nx])."""
+    ny, nx = _shape(ctx)
+    g = _c64(dl_drho, (ny, nx))
+    dth = np.zeros((2, nx))
+    dT = c_double()
+    df0 = np.zeros((9, ny, nx)) if want_df0 else None
+    _check(load().lbm_adjoint_backward(ctx, _dp(g), _dp(dth), ctypes.byref(dT),
+                                       _dp(df0) if want_df0 else None), "lbm_adjoint_backward")
+    return dth, dT.value, df0
+
+
+def lbm_adjoint_release(ctx):
+    _check(load().lbm_adjoint_release(ctx), "lbm_adjoint_release")
 
 
 def lbm_batch_config_default(**overrides) -> lbm_batch_config:
