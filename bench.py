@@ -307,6 +307,7 @@ def run_ours(args):
     node_bytes = 8 * w.nx * w.ny
 
     batched = None if args.batch_steps <= 0 else run_batched(args, stream)
+    adjoint = None if args.no_adjoint else run_adjoint(stream)
 
     if rank == 0:
         peak, peak_kind = _peaks()
@@ -348,6 +349,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk,
             "batched": batched,
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -432,6 +434,52 @@ def run_batched(args, stream):
     }
 
 
+def run_adjoint(stream):
+    """Gradient of the wall-angle inversion loss (256 x 128, 2000 steps, FP32)
+    in the 256 bottom-wall angles and T: recorded forward + reverse sweep,
+    against a plain forward of the same steps with lbm_step."""
+    from paper_1501_05430_gb300 import inputs as I
+    from paper_1501_05430_gb300 import lbm as L
+
+    ac = I.adjoint_case()
+    nx, ny = ac["nx"], ac["ny"]
+    eos = L.carnahan_starling(1.0, 4.0, 1.0)
+    T = ac["t_over_tc"] * L.lbm_eos_critical(eos)[0]
+    rv, rl = L.lbm_coexistence(eos, T)
+    theta = np.full((ny, nx), np.pi / 2)
+    theta[0] = ac["theta"]
+    rho0 = I.droplet_field(nx, ny, [ac["droplet"]], rv, rl, ac["width"])
+    p = L.lbm_params_default(precision=32, check_every=0)
+    out = {}
+    with L.Lbm(nx, ny, eos, T, ac["tau"], theta=theta, params=p, stream=stream) as s:
+        s.set_rho(rho0)
+        s.step(20)
+        s.set_rho(rho0)
+        s.sync()
+        t0 = time.perf_counter()
+        s.step(ac["steps"])
+        s.sync()
+        out["plain_forward_ms"] = (time.perf_counter() - t0) * 1e3
+        s.set_rho(rho0)
+        s.sync()
+        t0 = time.perf_counter()
+        L.lbm_adjoint_record(s.ctx, ac["steps"], ac["checkpoint_every"])
+        out["recorded_forward_ms"] = (time.perf_counter() - t0) * 1e3
+        h_t, W_t = I.profile(s.rho(), rv, rl)  # target: the same run (the loss is then zero; timing only)
+        _, g = I.profile_loss_grad(s.rho(), h_t + 0.1, W_t + 1.0, rv, rl)
+        t0 = time.perf_counter()
+        dth, dT, _ = L.lbm_adjoint_backward(s.ctx, g)
+        out["backward_ms"] = (time.perf_counter() - t0) * 1e3
+        L.lbm_adjoint_release(s.ctx)
+    out.update({
+        "workload": "wall-angle inversion, 256 x 128, CS T/Tc 0.7, tau 1, R0 40, FP32",
+        "steps": ac["steps"], "checkpoint_every": ac["checkpoint_every"], "parameters": nx + 1,
+        "gradient_cost_vs_plain_forward": (out["recorded_forward_ms"] + out["backward_ms"]) / out["plain_forward_ms"],
+        "finite": bool(np.isfinite(dth).all() and np.isfinite(dT)),
+    })
+    return out
+
+
 def _kernel_sha():
     import hashlib
 
@@ -449,6 +497,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
     ap.add_argument("--batch-steps", type=int, default=2000,
                     help="steps of the batched-sweep comparison (0 skips it)")
     ap.add_argument("--nx", type=int, default=None, help="workload width (default 4096)")
