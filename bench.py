@@ -375,7 +375,11 @@ def run_batched(args, stream):
     rho0 = [RN.initial_rho(w) for w in ws]
     for r, inst in zip(rho0, b.instances):
         inst.set_rho(r)
-    cfg = b.autotune(trial_steps=20)
+    if args.batch_shape:
+        th, stg, b0, b1, b2, b3, k = (int(v) for v in args.batch_shape.split(","))
+        cfg = L.lbm_batch_config_default(threads=th, stages=stg, band_rows=[b0, b1, b2, b3], steps_per_launch=k)
+    else:
+        cfg = b.autotune(trial_steps=20)
     cfg.graph_launches = max(2, 2 * (64 // (2 * cfg.steps_per_launch)))
     b.set_config(cfg)
     warm = cfg.graph_launches * cfg.steps_per_launch
@@ -498,6 +502,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
+    ap.add_argument("--batch-shape", default=None,
+                    help="fixed batched launch shape threads,stages,band0,band1,band2,band3,steps_per_launch "
+                         "(default: autotune)")
     ap.add_argument("--batch-steps", type=int, default=2000,
                     help="steps of the batched-sweep comparison (0 skips it)")
     ap.add_argument("--nx", type=int, default=None, help="workload width (default 4096)")
