@@ -1,0 +1,205 @@
+"""The paper's stationary-droplet experiments as presets, each run as one
+batched sweep (lbm_batch_*), with the measurements the paper reports.
+
+Setup shared by every preset (Sec. 3.1): the Eq. 11 EOS with the Table 1
+parameters of the chosen density ratio (rho_v = 1, rho_l = ratio), A = -0.6,
+kappa = 0.5 unless varied, the relaxation matrix diag(0, 1, ..., 1) (tau = 1),
+a semicircular droplet of radius 30 centred on the bottom wall.  The paper does
+not give its domain, run length or initial interface width: here 300 x 100
+nodes (a 15-degree cap of the semicircle's area is 180 nodes wide), 30,000
+steps and a tanh interface of width 10 by default (width 3 blows up at 15-45
+degrees at ratios 100 and 1000).  ``init="cap"`` starts from the circular cap
+of the semicircle's area at the set angle instead (a 150-degree droplet
+released as a semicircle bounces off the wall).
+
+  E1  Martys-Chen (Eq. 14), ratio 10, G_w in {-0.766, -1.1, -1.43, -1.77, -2.1, -2.43, -2.766}   Fig. 1
+  E2  Martys-Chen, ratio 100, G_w in {-2.666, -3.333, -4}                                       Fig. 2
+  E3  Martys-Chen, ratio 1000, G_w scaled from E2 by psi_l (Sec. 3.1: unstable when attached)
+  E4  Martys-Chen, ratio 10, density normal to the wall (liquid and vapour), G_w -0.766 / -2.43  Fig. 3
+  E5  Martys-Chen, ratio 10, G_w in {-1.1, -1.43, -2.1} x kappa in {0.5, 0.9, 0.98}            Fig. 4
+  E6  geometric (Eqs. 19-21), ratio 100, theta 15 deg, Eq. 19 only vs four iterations          Fig. 5
+  E7  geometric, ratio 100, theta in {15, 30, 45, 90, 135, 150} deg                             Fig. 6
+  E8  geometric, ratio 1000, the same angles                                                    Fig. 7
+  E9  geometric, ratio 100, density normal to the wall at theta 45 and 135 deg                  Fig. 8
+  E10 geometric, ratio 100, theta in {45, 90, 135} x kappa in {0.5, 0.9, 0.98}                  Fig. 9
+
+  python -m paper_1501_05430_gb300.experiments E7 [--steps 30000] [--width 10] [--init cap]
+
+Argument marshalling and measurement only: every step runs in liblbm's kernels.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+from dataclasses import dataclass, field
+from typing import Dict, List
+
+import numpy as np
+
+from . import inputs as I
+from . import lbm as L
+
+NX, NY, R0 = 300, 100, 30.0
+PROFILE_ROWS = 16
+
+
+@dataclass
+class Case:
+    name: str
+    ratio: int
+    wetting: int = L.LBM_WET_GEOMETRIC
+    theta_deg: float = 90.0
+    G_w: float = 0.0
+    kappa: float = 0.5
+    n_iter: int = 4
+    meta: Dict = field(default_factory=dict)
+
+    def eos(self):
+        r1, r2, tv, tm, tl = I.TABLE1[self.ratio]
+        return L.piecewise(tv, tm, tl, r1, r2)
+
+    def desc(self, nx=NX, ny=NY):
+        p = L.lbm_params_default(precision=32, kappa=self.kappa, G_w=self.G_w, wetting=self.wetting,
+                                 n_iter=self.n_iter, check_every=0)
+        theta = I.theta_field(nx, ny, np.deg2rad(self.theta_deg), np.pi / 2)
+        return dict(nx=nx, ny=ny, eos=self.eos(), T=0.0, tau=1.0, theta=theta, params=p)
+
+
+def _mc(ratio, gws, kappas=(0.5,), tag=""):
+    return [Case(f"{tag}MC ratio {ratio} G_w {g} kappa {k}", ratio, L.LBM_WET_MARTYS_CHEN, G_w=g, kappa=k,
+                 meta=dict(G_w=g, kappa=k)) for k in kappas for g in gws]
+
+
+def _geo(ratio, thetas, kappas=(0.5,), n_iter=4):
+    return [Case(f"geometric ratio {ratio} theta {t} kappa {k} n_iter {n_iter}", ratio, theta_deg=t, kappa=k,
+                 n_iter=n_iter, meta=dict(theta_set=t, kappa=k, n_iter=n_iter)) for k in kappas for t in thetas]
+
+
+def presets() -> Dict[str, List[Case]]:
+    # psi_l grows with the ratio (psi^2 = 2(rho/3 - p)); the Martys-Chen strengths
+    # of ratio 1000 are E2's scaled by psi_l(1000)/psi_l(100) (the paper gives none)
+    scale = _psi_l(1000) / _psi_l(100)
+    return {
+        "E1": _mc(10, (-0.766, -1.1, -1.43, -1.77, -2.1, -2.43, -2.766)),
+        "E2": _mc(100, (-2.666, -3.333, -4.0)),
+        "E3": _mc(1000, tuple(round(g * scale, 3) for g in (-2.666, -3.333, -4.0))),
+        "E4": _mc(10, (-0.766, -2.43)),
+        "E5": _mc(10, (-1.1, -1.43, -2.1), kappas=(0.5, 0.9, 0.98)),
+        "E6": _geo(100, (15.0,), n_iter=0) + _geo(100, (15.0,), n_iter=4),
+        "E7": _geo(100, (15.0, 30.0, 45.0, 90.0, 135.0, 150.0)),
+        "E8": _geo(1000, (15.0, 30.0, 45.0, 90.0, 135.0, 150.0)),
+        "E9": _geo(100, (45.0, 135.0)),
+        "E10": _geo(100, (45.0, 90.0, 135.0), kappas=(0.5, 0.9, 0.98)),
+    }
+
+
+def _psi_l(ratio):
+    r1, r2, tv, tm, tl = I.TABLE1[ratio]
+    rl = float(ratio)
+    p = r1 * tv + (r2 - r1) * tm + (rl - r2) * tl
+    return float(np.sqrt(2.0 * (rl / 3.0 - p)))
+
+
+def _walk(v, start, step, level):
+    """Offset from start (periodic, in the direction step = +1 or -1) of the
+    linear-interpolated point where v drops below level, or None."""
+    n = v.shape[0]
+    for k in range(n - 1):
+        a, b = v[(start + step * k) % n], v[(start + step * (k + 1)) % n]
+        if a >= level > b:
+            return k + (a - level) / (a - b)
+    return None
+
+
+def cap_above_layer(rho: np.ndarray, rho_mid: float, max_row: int = PROFILE_ROWS):
+    """Apparent angle of a droplet whose liquid does not reach the boundary row
+    (the depleted layer the Eq. 14 force leaves under a non-wetting droplet):
+    the circular-cap construction of lbm_contact_angle with the base on the
+    lowest row b where the droplet's centre column reaches rho_mid.  Returns
+    (theta_deg, H, L, b) or None."""
+    xc = int(np.argmax(rho[1:-1].sum(0)))
+    col = rho[:, xc]
+    rows = [y for y in range(1, max_row) if col[y] >= rho_mid]
+    if not rows:
+        return None
+    b = rows[0]
+    right = _walk(rho[b], xc, 1, rho_mid)
+    left = _walk(rho[b], xc, -1, rho_mid)
+    up = _walk(col[:-1], b, 1, rho_mid)
+    if right is None or left is None or up is None:
+        return None
+    Lb, H = right + left, up
+    return float(np.degrees(2.0 * np.arctan2(2.0 * H, Lb))), float(H), float(Lb), b
+
+
+def measure(inst, c: Case, rho_v: float, rho_l: float) -> dict:
+    """Status, apparent angle, max speed and the density normal to the wall in
+    the liquid (droplet centre column) and in the vapour (column 0).  When no
+    liquid touches the boundary row, the cap above the depleted layer is
+    measured too (theta_above_layer, base_row)."""
+    out = dict(case=c.name, **c.meta)
+    st = inst.status()
+    if st != 0:
+        out.update(status="unstable")
+        return out
+    rho = inst.rho()
+    rho_mid = 0.5 * (rho_v + rho_l)
+    try:
+        th, H, Lb = inst.contact_angle(0, 0, rho.shape[1])
+        out.update(status="stable", contact="cap", theta=float(np.degrees(th)), H=H, L=Lb)
+    except L.LbmError as e:
+        if e.status != L.LBM_ENOCONTACT:
+            raise
+        out.update(status="stable", contact="detached" if rho[1].max() < rho_mid else "film")
+        if out["contact"] == "detached":
+            cap = cap_above_layer(rho, rho_mid)
+            if cap is not None:
+                out.update(theta_above_layer=cap[0], base_row=cap[3])
+    xc = int(np.argmax(rho[1:-1].sum(0)))
+    out["max_u"] = inst.max_speed()
+    out["liquid_profile"] = [float(v) for v in rho[1:1 + PROFILE_ROWS, xc]]
+    out["vapour_profile"] = [float(v) for v in rho[1:1 + PROFILE_ROWS, 0]]
+    return out
+
+
+def initial_rho(c: Case, width: float, init: str = "semicircle"):
+    """The paper's initial semicircle of radius R0 on the bottom wall, or
+    (init = "cap") the circular cap of the same area at the set angle, which
+    starts the run near its equilibrium shape."""
+    rv, rl = L.lbm_coexistence(c.eos(), 0.0)
+    if init == "cap" and c.wetting == L.LBM_WET_GEOMETRIC:
+        t = np.deg2rad(c.theta_deg)
+        R = R0 * np.sqrt(0.5 * np.pi / (t - np.sin(t) * np.cos(t)))
+        return I.droplet_field(NX, NY, [(NX / 2.0, R, 1.0 - R * np.cos(t))], rv, rl, width), rv, rl
+    return I.droplet_field(NX, NY, [(NX / 2.0, R0, 0)], rv, rl, width), rv, rl
+
+
+def run(name: str, steps: int = 30000, width: float = 10.0, stream=None, cases=None,
+        init: str = "semicircle") -> List[dict]:
+    cases = cases if cases is not None else presets()[name]
+    descs = [c.desc() for c in cases]
+    with L.LbmBatch(descs, stream=stream) as b:
+        dens = []
+        for c, inst in zip(cases, b.instances):
+            rho, rv, rl = initial_rho(c, width, init)
+            inst.set_rho(rho)
+            dens.append((rv, rl))
+        b.step(steps)
+        return [measure(inst, c, rv, rl) for c, inst, (rv, rl) in zip(cases, b.instances, dens)]
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("preset", choices=list(presets()))
+    ap.add_argument("--steps", type=int, default=30000)
+    ap.add_argument("--width", type=float, default=10.0, help="initial tanh interface width")
+    ap.add_argument("--init", choices=["semicircle", "cap"], default="semicircle")
+    a = ap.parse_args(argv)
+    for r in run(a.preset, a.steps, a.width, init=a.init):
+        print(json.dumps(r))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
