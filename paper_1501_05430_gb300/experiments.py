@@ -24,6 +24,7 @@ released as a semicircle bounces off the wall).
   E10 geometric, ratio 100, theta in {45, 90, 135} x kappa in {0.5, 0.9, 0.98}                  Fig. 9
 
   python -m paper_1501_05430_gb300.experiments E7 [--steps 30000] [--width 10] [--init cap]
+  python -m paper_1501_05430_gb300.experiments calibrate [--targets 60,90,120] [--ratio 10]
 
 Argument marshalling and measurement only: every step runs in liblbm's kernels.
 """
@@ -189,13 +190,75 @@ def run(name: str, steps: int = 30000, width: float = 10.0, stream=None, cases=N
         return [measure(inst, c, rv, rl) for c, inst, (rv, rl) in zip(cases, b.instances, dens)]
 
 
+def _angle_of(r: dict) -> float:
+    """Apparent angle of a finished Martys-Chen case on the 0-180 deg scale:
+    a film is 0, a droplet lifted off the wall 180, a cap above a depleted
+    layer its angle there; NaN when unstable."""
+    if r["status"] != "stable":
+        return float("nan")
+    if r.get("contact") == "cap":
+        return r["theta"]
+    if r.get("contact") == "film":
+        return 0.0
+    return r.get("theta_above_layer", 180.0)
+
+
+def calibrate_gw(targets, ratio: int = 10, kappa: float = 0.5, lo: float = -0.8, hi: float = -2.8,
+                 steps: int = 5000, rounds: int = 5, points: int = 4, width: float = 10.0, stream=None):
+    """G_w giving each target angle (deg) with the Martys-Chen force (Eq. 14):
+    the measured angle falls as the wall attraction grows (-G_w), so each
+    round evaluates ``points`` interior values of every target's bracket in
+    one batch (all targets together) after ``steps`` steps and keeps the
+    sub-interval where the angle crosses the target.  Returns, per target,
+    dict(target, G_w, theta, reached, bracket): the evaluated G_w whose angle
+    came closest, that angle, whether it is within 2 deg, and the final
+    bracket (which closes on the stable edge when no stable G_w in [hi, lo]
+    reaches the target)."""
+    br = {t: [lo, hi] for t in targets}
+    last = {}
+    for _ in range(rounds):
+        cases, owner = [], []
+        for t in targets:
+            a, b = br[t]
+            for k in range(1, points + 1):
+                g = a + (b - a) * k / (points + 1)
+                cases.append(Case(f"calibrate {t} G_w {g:.5f}", ratio, L.LBM_WET_MARTYS_CHEN, G_w=g, kappa=kappa,
+                                  meta=dict(G_w=g, kappa=kappa)))
+                owner.append(t)
+        res = run("calibration", steps, width, stream, cases)
+        for t in targets:
+            a, b = br[t]
+            pts = [(a, 180.0)] + [(r["G_w"], _angle_of(r)) for r, o in zip(res, owner) if o == t] + [(b, 0.0)]
+            # first sub-interval (weak -> strong attraction) whose angles straddle the target
+            for (g0, t0), (g1, t1) in zip(pts[:-1], pts[1:]):
+                if np.isnan(t1):  # unstable from here on: the target is past the stable range
+                    br[t] = [g0, g1]
+                    break
+                if t0 >= t >= t1:
+                    br[t] = [g0, g1]
+                    break
+            last[t] = min((p for p in pts[1:-1] if not np.isnan(p[1])), key=lambda p: abs(p[1] - t),
+                          default=(float("nan"), float("nan")))
+    out = []
+    for t in targets:
+        g, th = last[t]
+        out.append(dict(target=t, G_w=g, theta=th, reached=bool(abs(th - t) <= 2.0), bracket=list(br[t])))
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("preset", choices=list(presets()))
+    ap.add_argument("preset", choices=list(presets()) + ["calibrate"])
+    ap.add_argument("--targets", default="60,90,120", help="calibrate: target angles (deg)")
+    ap.add_argument("--ratio", type=int, default=10, help="calibrate: Table 1 density ratio")
     ap.add_argument("--steps", type=int, default=30000)
     ap.add_argument("--width", type=float, default=10.0, help="initial tanh interface width")
     ap.add_argument("--init", choices=["semicircle", "cap"], default="semicircle")
     a = ap.parse_args(argv)
+    if a.preset == "calibrate":
+        for r in calibrate_gw([float(t) for t in a.targets.split(",")], ratio=a.ratio, width=a.width):
+            print(json.dumps(r))
+        return 0
     for r in run(a.preset, a.steps, a.width, init=a.init):
         print(json.dumps(r))
     return 0

@@ -134,3 +134,15 @@ def test_eq19_alone_and_four_iterations_agree_at_15_degrees(results):
     th = {r["n_iter"]: r["theta"] for r in res}
     assert abs(th[0] - th[4]) <= 1.0
     assert abs(th[4] - 15.0) <= 1.0
+
+
+def test_martys_chen_calibration_hits_90_degrees_at_ratio_10():
+    """G_w(theta) calibration (batched k-section at 5000 steps): 90 deg at
+    ratio 10 lies between the E1 strengths -1.43 (107 deg) and -1.77 (84 deg),
+    and re-running the calibrated G_w gives the angle within 2 deg."""
+    (r,) = E.calibrate_gw([90.0], ratio=10, rounds=4)
+    assert r["reached"], r
+    assert -1.9 < r["G_w"] < -1.3, r
+    (again,) = E.run("check", 5000, cases=[E.Case("check", 10, L.LBM_WET_MARTYS_CHEN, G_w=r["G_w"],
+                                                  meta=dict(G_w=r["G_w"]))])
+    assert abs(E._angle_of(again) - 90.0) <= 2.0, again
