@@ -51,7 +51,7 @@ struct Cfg {
   static constexpr int WIN = W + 4;                             // window columns c = -2 .. W+1
   static constexpr int MAIN_BYTES = 9 * W * 4;                  // 9 planes x W floats
   static constexpr int STAGE_BYTES = MAIN_BYTES + 2 * HALO_PAD;
-  static constexpr int MIN_CTAS = NC == 1 ? 8 : 5;             // register budget per thread
+  static constexpr int MIN_CTAS = NC == 1 ? 6 : 4;             // register budget per thread
 };
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per bounded wait
 
@@ -215,22 +215,24 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
   }
 
   // ---- row sweep --------------------------------------------------------------
-  // A stage is read twice: when its row enters the window (iteration i) and
-  // when that row is collided (iteration i+1, after the barrier).  It is free
-  // after the barrier of iteration i+2, so the producer refills up to
-  // (loads consumed by the end of iteration i-2) + S.
+  // A stage is read once, when its row enters the window (iteration i): each
+  // thread keeps the populations of its columns in registers until the row is
+  // collided in iteration i+1.  The stage is free after the barrier of
+  // iteration i, so the producer refills up to (loads consumed) + S.  Two
+  // register sets alternate between the "entering" and the "colliding" row
+  // (the loop body is instantiated twice with the sets swapped).
   Seq cs;
   cs.init(P, u0, u1);
-  int consumed = 0, cons_m1 = 0, cons_m2 = 0;  // loads consumed (after iterations i, i-1, i-2)
+  int consumed = 0;                             // loads consumed
   int get_stage = 0;                            // ring slot of the next load to consume
   unsigned get_phase = 0;                       // its mbarrier phase parity
-  int prev_stage = 0;
   int it = 0;
   bool bad = false;
   // thread t owns columns t, t + NCONS, ...: unit-stride shared-memory and
   // global accesses across the warp for each of them
+  float fA[NC][9], fB[NC][9];
 
-  while (cs.has) {
+  auto body = [&](float (&fin)[NC][9], const float (&fcol)[NC][9]) -> bool {
     const int v = cs.v;
     const int x0 = cs.strip * W;
     const int wr = min(W, P.nx - x0);
@@ -241,10 +243,8 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
     const bool hact = hidx >= 0 && (hidx < 2 || need2);
     const bool hact2 = hidx >= 0 && hidx < 2;  // halo columns that get a ghost value
     const bool cact = tid < wr;
-    int cur_stage = prev_stage;
     if (!cs.solid(P)) {
       const int s = get_stage;
-      cur_stage = s;
       const unsigned ph = get_phase;
       if (++get_stage == S) {
         get_stage = 0;
@@ -260,8 +260,10 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         const int c = tid + j * NCONS;
         if (c < wr) {
           const float *q = st + c;
-          float r = (((q[0] + q[W]) + (q[2 * W] + q[3 * W])) + ((q[4 * W] + q[5 * W]) + (q[6 * W] + q[7 * W]))) +
-                    q[8 * W];
+          float *fq = fin[j];
+#pragma unroll
+          for (int a = 0; a < 9; ++a) fq[a] = q[a * W];
+          float r = (((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7]))) + fq[8];
           const float4 e = eos_node(P, r);
           rcur[c + 2] = r;
           wcur[c + 2] = make_float2(e.y, e.z);
@@ -334,16 +336,15 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
       }
     }
     __syncthreads();
-    if (s_abort) break;
+    if (s_abort) return false;
 
-    // ---- collide row v-1 (its populations are still in stage prev_stage) ----
+    // ---- collide row v-1 (its populations are in registers since the last iteration) ----
     if (cact && v >= cs.ya + 1 && v <= cs.yb) {
       const int y = v - 1;
       const float2 *wm = win + (size_t)((it - 2) & 3) * WIN;  // row y-1
       const float2 *w0 = win + (size_t)((it - 1) & 3) * WIN;  // row y
       const float2 *wp = wcur;                                 // row y+1
       const float *r0w = winr + (size_t)((it - 1) & 3) * WIN;
-      const float *st = (const float *)(stage_base + (size_t)prev_stage * STAGE_BYTES);
       const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
       const bool wall_dn = P.walls && y == 1, wall_up = P.walls && y == P.ny - 2;
       // per-plane output pointers are warp-uniform; each store adds one 32-bit
@@ -367,10 +368,8 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         nb[6] = wp[i0 - 1];
         nb[7] = wm[i0 - 1];
         nb[8] = wm[i0 + 1];
-        float f[9], fs[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) f[a] = st[a * W + c];
-        collide_node<UNIT>(P, f, nb, r0w[i0], y, fs);
+        float fs[9];
+        collide_node<UNIT>(P, fcol[j], nb, r0w[i0], y, fs);
         // streaming with half-way bounce-back
         const int x = x0 + c;
         const unsigned xm = x == 0 ? P.nx - 1 : x - 1, xp = x == P.nx - 1 ? 0 : x + 1;
@@ -397,12 +396,12 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         }
       }
     }
-    prev_stage = cur_stage;
-    if (producer) issue_until(cons_m2 + S);
-    cons_m2 = cons_m1;
-    cons_m1 = consumed;
+    if (producer) issue_until(consumed + S);
     ++it;
     cs.next(P);
+    return cs.has;
+  };
+  while (body(fA, fB) && body(fB, fA)) {
   }
 
   if (s_abort && producer) {
@@ -463,9 +462,9 @@ int lbm_fused_plan(lbm_ctx *C) {
   // depth and CTAs per SM
   int nc = 2;
   if (const char *e = getenv("LBM_FUSED_COLS")) nc = atoi(e) == 1 ? 1 : 2;
-  int stages = 4;
+  int stages = 3;
   if (const char *e = getenv("LBM_FUSED_STAGES")) stages = atoi(e);
-  if (stages < 3 || stages > 12) stages = 4;
+  if (stages < 3 || stages > 12) stages = 3;
   const int W = nc * NCONS;
   for (int b = 0; b < 2; ++b) {
     if (!encode((CUtensorMap *)C->tmaps[2 * b], C->f[b], C->nx, C->ny, W)) return 0;
