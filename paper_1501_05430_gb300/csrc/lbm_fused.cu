@@ -3,24 +3,26 @@
 // One kernel launch performs the whole step of the pseudo-potential D2Q9 model
 // (Eqs. 1-6, 9-11, 14-17, 19-21):
 //
-//  * Work split: the grid is cut into strips of W = 128 columns; a "unit" is
-//    one fluid row of one strip.  The launch is persistent (a few CTAs per
-//    SM) and each CTA sweeps one contiguous, equally sized range of units,
-//    bottom to top inside each strip.
+//  * Work split: the grid is cut into strips of W = 256 columns; a "unit" is
+//    one fluid row of one strip.  The launch is persistent (4 CTAs of 128
+//    threads per SM) and each CTA sweeps one contiguous, equally sized range
+//    of units, bottom to top inside each strip.
 //  * Loads: one elected thread streams the rows of the CTA's range into a
 //    ring of shared-memory stages with TMA (cp.async.bulk.tensor, a 3-D
 //    tensor map over [9][ny][nx] with a box of W columns x 1 row x 9 planes),
 //    plus two 4-column halo boxes for the periodic x neighbours.  Completion is
 //    tracked with mbarriers; every wait is bounded in time and a timeout sets a
 //    device flag (LBM_ETIMEOUT) instead of hanging.
-//  * Per row: each thread owns one column, sums its 9 populations (rho), maps
-//    rho to U and psi (Eq. 10 with the Carnahan-Starling or Eq. 11 EOS) and
-//    writes them into a 4-row window; the ghost rows of Eqs. 19-21 are formed
-//    in the same window as soon as rows 1-2 (or ny-2, ny-3) are present.
-//    With the window holding rows y-1..y+1, row y is collided: Eq. 9 force,
-//    Eq. 17 tensor, MRT collision with the Eq. 6 forcing and Eq. 16 source,
-//    and the post-collision populations are pushed to the neighbours in the
-//    second distribution array (half-way bounce-back on the solid rows).
+//  * Per row: each thread owns columns t and t + 128 as one lane pair, keeps
+//    their 9 populations in registers, sums rho for both with packed FP32
+//    adds, maps rho to psi and psi^2 (Eq. 10 with the Carnahan-Starling or
+//    Eq. 11 EOS) and writes them into a 4-row window laid out in lane pairs;
+//    the ghost rows of Eqs. 19-21 are formed in the same window as soon as
+//    rows 1-2 (or ny-2, ny-3) are present.  With the window holding rows
+//    y-1..y+1, row y is collided, both columns per packed instruction: Eq. 9
+//    force, Eq. 17 tensor, MRT collision with the Eq. 6 forcing and Eq. 16
+//    source, and the post-collision populations are pushed to the neighbours
+//    in the second distribution array (half-way bounce-back on the solid rows).
 //  * Bytes: every population is read once from HBM and written once (72 B per
 //    node); halo columns and the two extra rows at range ends are re-read
 //    mostly from L2.  psi and U never go to HBM.
@@ -33,7 +35,8 @@
 
 namespace {
 
-using lbm_node::collide_node;
+using lbm_node::add2;
+using lbm_node::collide_node2;
 using lbm_node::eos_node;
 using lbm_node::ghost_node;
 using lbm_node::sqrt0;
@@ -49,9 +52,10 @@ template <int NC>
 struct Cfg {
   static constexpr int W = NC * NCONS;                          // columns per strip
   static constexpr int WIN = W + 4;                             // window columns c = -2 .. W+1
+  static constexpr int WP = NCONS + 4;                          // paired window entries i = -2 .. NCONS+1
   static constexpr int MAIN_BYTES = 9 * W * 4;                  // 9 planes x W floats
   static constexpr int STAGE_BYTES = MAIN_BYTES + 2 * HALO_PAD;
-  static constexpr int MIN_CTAS = NC == 1 ? 6 : 4;             // register budget per thread
+  static constexpr int MIN_CTAS = 4;                            // register budget per thread
 };
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per bounded wait
 
@@ -144,15 +148,21 @@ struct Seq {
 template <bool UNIT, int NC>
 __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
     k_fused(const __grid_constant__ CUtensorMap tm_main, const __grid_constant__ CUtensorMap tm_halo, FusedArgs P) {
-  constexpr int W = Cfg<NC>::W, WIN = Cfg<NC>::WIN, MAIN_BYTES = Cfg<NC>::MAIN_BYTES;
+  static_assert(NC == 2, "two columns per thread: one lane pair");
+  constexpr int W = Cfg<NC>::W, WIN = Cfg<NC>::WIN, WP = Cfg<NC>::WP, MAIN_BYTES = Cfg<NC>::MAIN_BYTES;
   constexpr int STAGE_BYTES = Cfg<NC>::STAGE_BYTES;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA destinations must be 128-byte aligned in shared memory
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int S = P.stages;
   unsigned char *stage_base = smem;
-  float2 *win = (float2 *)(smem + (size_t)S * STAGE_BYTES);  // [NSLOT][WIN]: (psi, psi^2)
-  float *winr = (float *)(win + NSLOT * WIN);                // [NSLOT][WIN]: rho
+  // window rows: psi and psi^2 in lane pairs -- entry i holds columns i and
+  // i + NCONS, i in [-2, NCONS + 1] at index i + 2 -- so that a thread's two
+  // columns (t, t + NCONS) and their x neighbours are one 64-bit load each;
+  // rho in column order (column c at c + 2, c in [-2, W + 1])
+  float2 *wpsi = (float2 *)(smem + (size_t)S * STAGE_BYTES);  // [NSLOT][WP]
+  float2 *wsq = wpsi + NSLOT * WP;                            // [NSLOT][WP]
+  float *winr = (float *)(wsq + NSLOT * WP);                  // [NSLOT][WIN]
   unsigned long long *bars = (unsigned long long *)(winr + NSLOT * WIN);
   volatile int &s_abort = *(volatile int *)(bars + S);
 
@@ -216,11 +226,12 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
 
   // ---- row sweep --------------------------------------------------------------
   // A stage is read once, when its row enters the window (iteration i): each
-  // thread keeps the populations of its columns in registers until the row is
-  // collided in iteration i+1.  The stage is free after the barrier of
-  // iteration i, so the producer refills up to (loads consumed) + S.  Two
-  // register sets alternate between the "entering" and the "colliding" row
-  // (the loop body is instantiated twice with the sets swapped).
+  // thread keeps the populations of its two columns in registers (lane pairs)
+  // until the row is collided in iteration i+1.  The stage is free after the
+  // barrier of iteration i, so the producer refills up to (loads consumed) +
+  // S.  Two register sets alternate between the "entering" and the
+  // "colliding" row (the loop body is instantiated twice with the sets
+  // swapped).
   Seq cs;
   cs.init(P, u0, u1);
   int consumed = 0;                             // loads consumed
@@ -228,21 +239,34 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
   unsigned get_phase = 0;                       // its mbarrier phase parity
   int it = 0;
   bool bad = false;
-  // thread t owns columns t, t + NCONS, ...: unit-stride shared-memory and
+  // thread t owns columns t and t + NCONS: unit-stride shared-memory and
   // global accesses across the warp for each of them
-  float fA[NC][9], fB[NC][9];
+  float2 fA[9], fB[9];
+  // (psi, psi^2) of column c into a window row pair: lane 0 of entry c and/or
+  // lane 1 of entry c - NCONS
+  auto put = [&](float2 *ps, float2 *sq, int c, float p, float q) {
+    if (c <= NCONS + 1) {
+      ps[c + 2].x = p;
+      sq[c + 2].x = q;
+    }
+    if (c >= NCONS - 2) {
+      ps[c - NCONS + 2].y = p;
+      sq[c - NCONS + 2].y = q;
+    }
+  };
 
-  auto body = [&](float (&fin)[NC][9], const float (&fcol)[NC][9]) -> bool {
+  auto body = [&](float2 (&fin)[9], const float2 (&fcol)[9]) -> bool {
     const int v = cs.v;
     const int x0 = cs.strip * W;
     const int wr = min(W, P.nx - x0);
-    float2 *wcur = win + (size_t)(it & 3) * WIN;
+    float2 *pcur = wpsi + (size_t)(it & 3) * WP, *qcur = wsq + (size_t)(it & 3) * WP;
     float *rcur = winr + (size_t)(it & 3) * WIN;
     const bool need2 = P.walls && geo && ((v == 1 && cs.ya == 1) || (v == P.ny - 2 && cs.yb == P.ny - 1));
     const int hc = hidx == 0 ? -1 : hidx == 1 ? wr : hidx == 2 ? -2 : wr + 1;
     const bool hact = hidx >= 0 && (hidx < 2 || need2);
     const bool hact2 = hidx >= 0 && hidx < 2;  // halo columns that get a ghost value
-    const bool cact = tid < wr;
+    const int c0 = tid, c1 = tid + NCONS;
+    const bool act0 = c0 < wr, act1 = c1 < wr;  // act1 implies act0
     if (!cs.solid(P)) {
       const int s = get_stage;
       const unsigned ph = get_phase;
@@ -255,19 +279,23 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         atomicOr(P.flag + 1, 1);
       }
       const float *st = (const float *)(stage_base + (size_t)s * STAGE_BYTES);
+      if (act0) {
+        const float *q0 = st + c0, *q1 = st + (act1 ? c1 : c0);
 #pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        const int c = tid + j * NCONS;
-        if (c < wr) {
-          const float *q = st + c;
-          float *fq = fin[j];
-#pragma unroll
-          for (int a = 0; a < 9; ++a) fq[a] = q[a * W];
-          float r = (((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7]))) + fq[8];
-          const float4 e = eos_node(P, r);
-          rcur[c + 2] = r;
-          wcur[c + 2] = make_float2(e.y, e.z);
-          bad |= !(r > 0.0f) || r > P.rho_max;
+        for (int a = 0; a < 9; ++a) fin[a] = make_float2(q0[a * W], q1[a * W]);
+        // rho of both columns, summed in the same order for each
+        const float2 r = add2(add2(add2(add2(fin[0], fin[1]), add2(fin[2], fin[3])),
+                                   add2(add2(fin[4], fin[5]), add2(fin[6], fin[7]))),
+                              fin[8]);
+        const float4 e0 = eos_node(P, r.x);
+        rcur[c0 + 2] = r.x;
+        put(pcur, qcur, c0, e0.y, e0.z);
+        bad |= !(r.x > 0.0f) || r.x > P.rho_max;
+        if (act1) {
+          const float4 e1 = eos_node(P, r.y);
+          rcur[c1 + 2] = r.y;
+          put(pcur, qcur, c1, e1.y, e1.z);
+          bad |= !(r.y > 0.0f) || r.y > P.rho_max;
         }
       }
       if (hact) {
@@ -277,13 +305,14 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
                   src[8 * HB];
         const float4 e = eos_node(P, r);
         rcur[hc + 2] = r;
-        wcur[hc + 2] = make_float2(e.y, e.z);
+        put(pcur, qcur, hc, e.y, e.z);
       }
       ++consumed;
       // bottom ghost row (Eqs. 19-21): rows 1 and 2 are now in the window
       if (P.walls && geo && cs.ya == 1 && v == 2) {
         const float *r1w = winr + (size_t)((it - 1) & 3) * WIN;  // row 1 densities
-        float2 *gw = win + (size_t)((it - 2) & 3) * WIN;         // row 0
+        float2 *gp = wpsi + (size_t)((it - 2) & 3) * WP;         // row 0
+        float2 *gq = wsq + (size_t)((it - 2) & 3) * WP;
         float *gr = winr + (size_t)((it - 2) & 3) * WIN;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
@@ -291,7 +320,7 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
           if (c < wr) {
             const float4 e = ghost_node(P, r1w, rcur, c, x0 + c, 0);
             gr[c + 2] = e.x;
-            gw[c + 2] = make_float2(e.y, e.z);
+            put(gp, gq, c, e.y, e.z);
           }
         }
         if (hact2) {
@@ -299,7 +328,7 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
           gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
           const float4 e = ghost_node(P, r1w, rcur, hc, gx, 0);
           gr[hc + 2] = e.x;
-          gw[hc + 2] = make_float2(e.y, e.z);
+          put(gp, gq, hc, e.y, e.z);
         }
       }
     } else {
@@ -314,24 +343,24 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         if (c < wr) {
           if (!geo) {
             rcur[c + 2] = 0.0f;
-            wcur[c + 2] = make_float2(0.0f, 0.0f);
+            put(pcur, qcur, c, 0.0f, 0.0f);
           } else if (top) {
             const float4 e = ghost_node(P, r1w, r2w, c, x0 + c, 1);
             rcur[c + 2] = e.x;
-            wcur[c + 2] = make_float2(e.y, e.z);
+            put(pcur, qcur, c, e.y, e.z);
           }
         }
       }
       if (hact2) {
         if (!geo) {
           rcur[hc + 2] = 0.0f;
-          wcur[hc + 2] = make_float2(0.0f, 0.0f);
+          put(pcur, qcur, hc, 0.0f, 0.0f);
         } else if (top) {
           int gx = x0 + hc;
           gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
           const float4 e = ghost_node(P, r1w, r2w, hc, gx, 1);
           rcur[hc + 2] = e.x;
-          wcur[hc + 2] = make_float2(e.y, e.z);
+          put(pcur, qcur, hc, e.y, e.z);
         }
       }
     }
@@ -339,11 +368,11 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
     if (s_abort) return false;
 
     // ---- collide row v-1 (its populations are in registers since the last iteration) ----
-    if (cact && v >= cs.ya + 1 && v <= cs.yb) {
+    if (act0 && v >= cs.ya + 1 && v <= cs.yb) {
       const int y = v - 1;
-      const float2 *wm = win + (size_t)((it - 2) & 3) * WIN;  // row y-1
-      const float2 *w0 = win + (size_t)((it - 1) & 3) * WIN;  // row y
-      const float2 *wp = wcur;                                 // row y+1
+      const float2 *pm = wpsi + (size_t)((it - 2) & 3) * WP, *qm = wsq + (size_t)((it - 2) & 3) * WP;  // row y-1
+      const float2 *p0 = wpsi + (size_t)((it - 1) & 3) * WP, *q0 = wsq + (size_t)((it - 1) & 3) * WP;  // row y
+      const float2 *pp = pcur, *qp = qcur;                                                               // row y+1
       const float *r0w = winr + (size_t)((it - 1) & 3) * WIN;
       const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
       const bool wall_dn = P.walls && y == 1, wall_up = P.walls && y == P.ny - 2;
@@ -353,48 +382,58 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
       float *const o4p = o3p + n, *const o5p = o4p + n, *const o6p = o5p + n, *const o7p = o6p + n;
       float *const o8p = o7p + n;
       const unsigned ry = (unsigned)y * P.nx, rym = (unsigned)ym * P.nx, ryp = (unsigned)yp * P.nx;
-#pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        const int c = tid + j * NCONS;
-        if (c >= wr) break;
-        const int i0 = c + 2;
-        float2 nb[9];
-        nb[0] = w0[i0];
-        nb[1] = w0[i0 + 1];
-        nb[2] = wp[i0];
-        nb[3] = w0[i0 - 1];
-        nb[4] = wm[i0];
-        nb[5] = wp[i0 + 1];
-        nb[6] = wp[i0 - 1];
-        nb[7] = wm[i0 - 1];
-        nb[8] = wm[i0 + 1];
-        float fs[9];
-        collide_node<UNIT>(P, fcol[j], nb, r0w[i0], y, fs);
-        // streaming with half-way bounce-back
-        const int x = x0 + c;
+      // streaming with half-way bounce-back of node x's post-collision populations
+      auto push = [&](int x, float f0, float f1, float f2, float f3, float f4, float f5, float f6, float f7,
+                      float f8) {
         const unsigned xm = x == 0 ? P.nx - 1 : x - 1, xp = x == P.nx - 1 ? 0 : x + 1;
-        o0p[ry + x] = fs[0];
-        o1p[ry + xp] = fs[1];
-        o3p[ry + xm] = fs[3];
+        o0p[ry + x] = f0;
+        o1p[ry + xp] = f1;
+        o3p[ry + xm] = f3;
         if (wall_up) {
-          o4p[ry + x] = fs[2];
-          o7p[ry + x] = fs[5];
-          o8p[ry + x] = fs[6];
+          o4p[ry + x] = f2;
+          o7p[ry + x] = f5;
+          o8p[ry + x] = f6;
         } else {
-          o2p[ryp + x] = fs[2];
-          o5p[ryp + xp] = fs[5];
-          o6p[ryp + xm] = fs[6];
+          o2p[ryp + x] = f2;
+          o5p[ryp + xp] = f5;
+          o6p[ryp + xm] = f6;
         }
         if (wall_dn) {
-          o2p[ry + x] = fs[4];
-          o5p[ry + x] = fs[7];
-          o6p[ry + x] = fs[8];
+          o2p[ry + x] = f4;
+          o5p[ry + x] = f7;
+          o6p[ry + x] = f8;
         } else {
-          o4p[rym + x] = fs[4];
-          o7p[rym + xm] = fs[7];
-          o8p[rym + xp] = fs[8];
+          o4p[rym + x] = f4;
+          o7p[rym + xm] = f7;
+          o8p[rym + xp] = f8;
         }
-      }
+      };
+      // both columns at once with the packed FP32 instructions (the second
+      // lane is computed even past a ragged strip end; it is not stored)
+      const int i = tid + 2;
+      float2 pn[9], qn[9], fs2[9];
+      pn[0] = p0[i];
+      qn[0] = q0[i];
+      pn[1] = p0[i + 1];
+      qn[1] = q0[i + 1];
+      pn[2] = pp[i];
+      qn[2] = qp[i];
+      pn[3] = p0[i - 1];
+      qn[3] = q0[i - 1];
+      pn[4] = pm[i];
+      qn[4] = qm[i];
+      pn[5] = pp[i + 1];
+      qn[5] = qp[i + 1];
+      pn[6] = pp[i - 1];
+      qn[6] = qp[i - 1];
+      pn[7] = pm[i - 1];
+      qn[7] = qm[i - 1];
+      pn[8] = pm[i + 1];
+      qn[8] = qm[i + 1];
+      collide_node2<UNIT>(P, fcol, pn, qn, make_float2(r0w[c0 + 2], r0w[c1 + 2]), y, fs2);
+      push(x0 + c0, fs2[0].x, fs2[1].x, fs2[2].x, fs2[3].x, fs2[4].x, fs2[5].x, fs2[6].x, fs2[7].x, fs2[8].x);
+      if (act1)
+        push(x0 + c1, fs2[0].y, fs2[1].y, fs2[2].y, fs2[3].y, fs2[4].y, fs2[5].y, fs2[6].y, fs2[7].y, fs2[8].y);
     }
     if (producer) issue_until(consumed + S);
     ++it;
@@ -441,16 +480,15 @@ bool encode(CUtensorMap *m, void *base, int nx, int ny, int boxw) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NC>
+constexpr int kNC = 2;  // columns per thread
+
 size_t smem_bytes(int stages) {
-  return 128 + (size_t)stages * Cfg<NC>::STAGE_BYTES + (size_t)NSLOT * Cfg<NC>::WIN * (sizeof(float2) + sizeof(float)) +
-         (size_t)stages * 8 + 16;
+  using C = Cfg<kNC>;
+  return 128 + (size_t)stages * C::STAGE_BYTES + (size_t)NSLOT * C::WP * 2 * sizeof(float2) +
+         (size_t)NSLOT * C::WIN * sizeof(float) + (size_t)stages * 8 + 16;
 }
 
-const void *kernel_ptr(bool unit, int nc) {
-  if (nc == 1) return unit ? (const void *)k_fused<true, 1> : (const void *)k_fused<false, 1>;
-  return unit ? (const void *)k_fused<true, 2> : (const void *)k_fused<false, 2>;
-}
+const void *kernel_ptr(bool unit) { return unit ? (const void *)k_fused<true, kNC> : (const void *)k_fused<false, kNC>; }
 
 }  // namespace
 
@@ -458,10 +496,8 @@ int lbm_fused_plan(lbm_ctx *C) {
   C->fused_ok = 0;
   if (C->precision != 32 || (C->nx % 4) != 0) return 0;
   static_assert(sizeof(CUtensorMap) <= sizeof(C->tmaps[0]), "tensor map storage");
-  // tuning knobs (defaults measured on GB300): columns per thread, TMA ring
-  // depth and CTAs per SM
-  int nc = 2;
-  if (const char *e = getenv("LBM_FUSED_COLS")) nc = atoi(e) == 1 ? 1 : 2;
+  // tuning knobs (defaults measured on GB300): TMA ring depth and CTAs per SM
+  const int nc = kNC;
   int stages = 3;
   if (const char *e = getenv("LBM_FUSED_STAGES")) stages = atoi(e);
   if (stages < 3 || stages > 12) stages = 3;
@@ -470,11 +506,11 @@ int lbm_fused_plan(lbm_ctx *C) {
     if (!encode((CUtensorMap *)C->tmaps[2 * b], C->f[b], C->nx, C->ny, W)) return 0;
     if (!encode((CUtensorMap *)C->tmaps[2 * b + 1], C->f[b], C->nx, C->ny, HB)) return 0;
   }
-  size_t smem = nc == 1 ? smem_bytes<1>(stages) : smem_bytes<2>(stages);
+  size_t smem = smem_bytes(stages);
   // the diag(0,1,...,1) relaxation of Sec. 3.1 takes the specialised collision
   const lbm_dev_params &D = C->dp;
   C->fused_unit = D.s[1] == 1.0 && D.s[2] == 1.0 && D.s[4] == 1.0 && D.s[7] == 1.0;
-  const void *kern = kernel_ptr(C->fused_unit, nc);
+  const void *kern = kernel_ptr(C->fused_unit);
   int dev = 0, nsm = 0, occ = 0, optin = 0;
   cudaGetDevice(&dev);
   // the attribute is per kernel, not per context: allow the device maximum so
@@ -558,13 +594,8 @@ cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches) {
   const CUtensorMap *tm = (const CUtensorMap *)C->tmaps[2 * src];
   const CUtensorMap *th = (const CUtensorMap *)C->tmaps[2 * src + 1];
   const dim3 grid(C->tile_blocks), block(NCONS);
-  if (C->fused_cols == 1) {
-    if (C->fused_unit) k_fused<true, 1><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
-    else k_fused<false, 1><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
-  } else {
-    if (C->fused_unit) k_fused<true, 2><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
-    else k_fused<false, 2><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
-  }
+  if (C->fused_unit) k_fused<true, kNC><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
+  else k_fused<false, kNC><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
   ++*launches;
   return cudaGetLastError();
 }

@@ -161,4 +161,109 @@ __device__ __forceinline__ void collide_node(const PT &P, const float *f, const 
   fs[8] = (Bdg + X2) - (Y2 + r8);
 }
 
+
+// ---- two nodes at once ------------------------------------------------------
+// The same node arithmetic on lane pairs (two nodes of one row that a thread
+// owns) with the packed FP32 instructions of sm_100+: one instruction issues
+// the operation for both nodes.  Each lane is an IEEE single-precision
+// operation; subtraction is fma(b, -1, a), which rounds like a - b.
+
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// f[9], psi[9], psi2[9]: lane pairs of the populations and of the neighbour
+// values (psi, psi^2) at x+e_0..x+e_8; rho: the two densities; fs: f*.
+template <bool UNIT, class PT>
+__device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, const float2 *psi, const float2 *psi2,
+                                              float2 rho, int y, float2 *fs) {
+  const float2 w1 = bc2(1.0f / 3.0f), w2 = bc2(1.0f / 12.0f);
+  const float2 p0 = psi[0];
+  const float2 c1 = mul2(bc2(P.omA), p0), hA = bc2(P.halfA);
+  float2 g[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) g[k] = fma2(c1, psi[k], mul2(hA, psi2[k]));
+  const float2 gd57 = sub2(g[5], g[7]), gd86 = sub2(g[8], g[6]);
+  float2 Fx = fma2(w1, sub2(g[1], g[3]), mul2(w2, add2(gd57, gd86)));
+  float2 Fy = fma2(w1, sub2(g[2], g[4]), mul2(w2, sub2(gd57, gd86)));
+  if (P.wetting == LBM_WET_MARTYS_CHEN && P.walls) {
+    const float ssy = (y == 1 ? -0.5f : 0.0f) + (y == P.ny - 2 ? 0.5f : 0.0f);
+    Fy = fma2(mul2(bc2(-P.Gw), p0), bc2(ssy), Fy);
+  }
+  const float2 gs57 = add2(g[5], g[7]), gs68 = add2(g[6], g[8]);
+  const float2 gq = mul2(w2, fma2(bc2(-4.0f), g[0], add2(gs57, gs68)));
+  const float2 pre = bc2(P.pre), m2 = bc2(-2.0f);
+  const float2 Qxx = mul2(pre, fma2(w1, fma2(m2, g[0], add2(g[1], g[3])), gq));
+  const float2 Qyy = mul2(pre, fma2(w1, fma2(m2, g[0], add2(g[2], g[4])), gq));
+  const float2 Qxy = mul2(pre, mul2(w2, sub2(gs57, gs68)));
+  const float2 s13 = sub2(f[1], f[3]), s24 = sub2(f[2], f[4]);
+  const float2 d57 = sub2(f[5], f[7]), d86 = sub2(f[8], f[6]);
+  const float2 jx = add2(s13, add2(d57, d86));
+  const float2 jy = add2(s24, sub2(d57, d86));
+  const float2 ir = make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
+  const float2 half = bc2(0.5f);
+  const float2 vx = mul2(fma2(half, Fx, jx), ir), vy = mul2(fma2(half, Fy, jy), ir);
+  const float2 rvx = mul2(rho, vx), rvy = mul2(rho, vy);
+  const float2 v2 = fma2(vx, vx, mul2(vy, vy));
+  const float2 vF = fma2(vx, Fx, mul2(vy, Fy));
+  const float2 sQ = add2(Qxx, Qyy), dQ = sub2(Qxx, Qyy);
+  const float2 one = bc2(1.0f), three = bc2(3.0f), mthree = bc2(-3.0f), mone = bc2(-1.0f);
+  float2 es, epss, qxs, qys, pxxs, pxys;
+  if (UNIT) {
+    es = fma2(rho, fma2(three, v2, bc2(-2.0f)), fma2(three, vF, mul2(bc2(1.5f), sQ)));
+    epss = fma2(rho, fma2(mthree, v2, one), mul2(mthree, vF));
+    qxs = mul2(mone, fma2(half, Fx, rvx));
+    qys = mul2(mone, fma2(half, Fy, rvy));
+    // rvx vx - rvy vy + vx Fx - vy Fy - (Qxx - Qyy)
+    pxxs = fma2(vx, add2(rvx, Fx), mul2(mone, fma2(vy, add2(rvy, Fy), dQ)));
+    // rvx vy + (vx Fy + vy Fx)/2 - Qxy
+    pxys = fma2(rvx, vy, sub2(mul2(half, fma2(vx, Fy, mul2(vy, Fx))), Qxy));
+  } else {
+    const float2 a13 = add2(f[1], f[3]), a24 = add2(f[2], f[4]);
+    const float2 ax = add2(a13, a24), dg = add2(add2(f[5], f[6]), add2(f[7], f[8]));
+    const float2 me = fma2(bc2(-4.0f), f[0], fma2(bc2(2.0f), dg, mul2(mone, ax)));
+    const float2 meps = fma2(bc2(4.0f), f[0], fma2(m2, ax, dg));
+    const float2 mqx = fma2(m2, s13, add2(d57, d86));
+    const float2 mqy = fma2(m2, s24, sub2(d57, d86));
+    const float2 mpxx = sub2(a13, a24);
+    const float2 mpxy = sub2(add2(f[5], f[7]), add2(f[6], f[8]));
+    const float2 se = bc2(P.se), seps = bc2(P.seps), sq = bc2(P.sq), snu = bc2(P.snu);
+    // m* = m - s (m - m_eq) + (1 - s/2) S + C
+    const float2 eeq = mul2(rho, fma2(three, v2, bc2(-2.0f)));
+    const float2 epseq = mul2(rho, fma2(mthree, v2, one));
+    es = add2(fma2(mul2(bc2(-1.0f), se), sub2(me, eeq), me), fma2(bc2(P.he * 6.0f), vF, mul2(bc2(1.5f * P.se), sQ)));
+    epss = sub2(fma2(mul2(mone, seps), sub2(meps, epseq), meps), mul2(bc2(P.heps * 6.0f), vF));
+    qxs = sub2(fma2(mul2(mone, sq), add2(mqx, rvx), mqx), mul2(bc2(P.hq), Fx));
+    qys = sub2(fma2(mul2(mone, sq), add2(mqy, rvy), mqy), mul2(bc2(P.hq), Fy));
+    const float2 pxxeq = fma2(rvx, vx, mul2(mone, mul2(rvy, vy)));
+    pxxs = add2(fma2(mul2(mone, snu), sub2(mpxx, pxxeq), mpxx),
+                fma2(bc2(P.hnu * 2.0f), fma2(vx, Fx, mul2(mone, mul2(vy, Fy))), mul2(mul2(mone, snu), dQ)));
+    pxys = add2(fma2(mul2(mone, snu), sub2(mpxy, mul2(rvx, vy)), mpxy),
+                fma2(bc2(P.hnu), fma2(vx, Fy, mul2(vy, Fx)), mul2(mul2(mone, snu), Qxy)));
+  }
+  const float2 jxs = add2(jx, Fx), jys = add2(jy, Fy);
+  const float2 c9 = bc2(1.0f / 9.0f);
+  float2 r0 = mul2(rho, c9);
+  r0 = fma2(fma2(bc2(-9.0f), r0, rho), c9, r0);
+  const float2 i36 = bc2(1.0f / 36.0f), i6 = bc2(1.0f / 6.0f), i12 = bc2(1.0f / 12.0f), q4 = bc2(0.25f);
+  const float2 r1 = mul2(es, i36), r2 = mul2(epss, i36);
+  const float2 r3 = mul2(jxs, i6), r4 = mul2(qxs, i12), r5 = mul2(jys, i6), r6 = mul2(qys, i12);
+  const float2 r7 = mul2(pxxs, q4), r8 = mul2(pxys, q4);
+  fs[0] = fma2(bc2(4.0f), sub2(r2, r1), r0);
+  const float2 Aax = fma2(m2, r2, sub2(r0, r1));
+  const float2 Bdg = fma2(bc2(2.0f), r1, add2(r0, r2));
+  const float2 X1 = fma2(m2, r4, r3), Y1 = fma2(m2, r6, r5);
+  fs[1] = add2(add2(Aax, X1), r7);
+  fs[3] = add2(sub2(Aax, X1), r7);
+  fs[2] = sub2(add2(Aax, Y1), r7);
+  fs[4] = sub2(sub2(Aax, Y1), r7);
+  const float2 X2 = add2(r3, r4), Y2 = add2(r5, r6);
+  fs[5] = add2(add2(Bdg, X2), add2(Y2, r8));
+  fs[6] = add2(sub2(Bdg, X2), sub2(Y2, r8));
+  fs[7] = sub2(sub2(Bdg, X2), sub2(Y2, r8));
+  fs[8] = sub2(add2(Bdg, X2), add2(Y2, r8));
+}
+
 }  // namespace lbm_node

@@ -124,7 +124,9 @@ def test_graph_replays_are_counted_and_match_direct_launches():
 
 def test_batch_equals_lone_fused_context():
     """The 400 x 200 single-droplet workload inside a batch against the same
-    case run alone by lbm_step's fused kernel (same node arithmetic)."""
+    case run alone by lbm_step's fused kernel: the same node arithmetic, except
+    that the fused kernel evaluates its two columns per thread with packed
+    two-lane FP32 instructions (same operations, other rounding order)."""
     w = I.single_droplet(60.0)
     c = Case(w.nx, w.ny, t_over_tc=w.t_over_tc, tau=w.tau, theta=w.theta, rates=w.rates, eos=w.eos,
              precision=32, kernel=L.LBM_KERNEL_FUSED)
@@ -140,7 +142,7 @@ def test_batch_equals_lone_fused_context():
         b.step(500)
         lone.step(500)
         rb, rl = b[0].rho(), lone.rho()
-        assert np.abs(rb - rl).max() <= 1e-6 * np.abs(rl).max()
+        assert np.abs(rb - rl).max() <= 1e-5 * np.abs(rl).max()
     _close(others)
     c.orc.close()
 
