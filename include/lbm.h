@@ -318,8 +318,8 @@ int lbm_adjoint_release(lbm_ctx *ctx);
  * advances every instance by steps_per_launch steps, and the CTAs that share
  * an instance meet at a per-instance barrier between its steps (no barrier
  * across instances).  Per node the arithmetic is that of lbm_step's FP32
- * kernel, so the per-instance results agree with a lone context to FP32
- * rounding. */
+ * fused kernel, so an instance gives the same bits as a lone context that
+ * runs the fused kernel. */
 typedef struct lbm_batch lbm_batch;
 
 typedef struct {
@@ -332,8 +332,8 @@ typedef struct {
 
 /* Launch shape.  Zero fields take the defaults in brackets. */
 typedef struct {
-  int threads;           /* threads per CTA, 128 or 256 [256]; each thread owns
-                            columns t, t + threads, ... of a row */
+  int threads;           /* threads per CTA: 256 (the one shape) [256]; thread t owns
+                            columns t and t + 256 of a row */
   int ctas_per_sm;       /* cap on resident CTAs per SM [occupancy maximum] */
   int stages;            /* row stages of the shared-memory copy ring, 3..6 [4] */
   int band_rows[4];      /* fluid rows per work item for nx in (0,128], (128,256],

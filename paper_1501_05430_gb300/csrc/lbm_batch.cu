@@ -16,13 +16,18 @@
 // batch abort word, and every CTA leaves at its next entry.  Instances never
 // wait on each other.
 //
-// Rows are streamed through a ring of shared-memory stages with 16-byte
-// cp.async copies that bypass L1 (.cg), so rows written by other CTAs in the
-// previous step are read from L2 after the barrier's acquire.  Per row the
-// node arithmetic is the one of the single-domain fused kernel
-// (lbm_node.cuh): rho, EOS, ghost rows (Eqs. 19-21), force (Eq. 9, Eq. 14),
-// Eq. 17 tensor, MRT collision with the Eq. 6 forcing and Eq. 16 source, push
-// streaming with half-way bounce-back.
+// Rows are streamed through a ring of shared-memory stages by one-dimensional
+// bulk copies (cp.async.bulk, 9 per row, one per plane) that one thread
+// issues, completing on an mbarrier per stage; after acquiring an instance's
+// barrier that thread orders the previous step's generic stores (of this and
+// other CTAs) before its asynchronous-proxy reads with fence.proxy.async.
+// Thread t owns columns t and t + 256 as one lane pair: rho of both with
+// packed adds, psi and psi^2 written to a window laid out in lane pairs, and
+// the node arithmetic of lbm_node.cuh in its packed two-node form -- the same
+// per-node operations as the single-domain fused kernel, so a batch instance
+// and a lone context produce the same bits: rho, EOS, ghost rows (Eqs. 19-21),
+// force (Eq. 9, Eq. 14), Eq. 17 tensor, MRT collision with the Eq. 6 forcing
+// and Eq. 16 source, push streaming with half-way bounce-back.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -36,12 +41,15 @@
 
 namespace {
 
-using lbm_node::collide_node;
+using lbm_node::add2;
+using lbm_node::collide_node2;
 using lbm_node::eos_node;
 using lbm_node::ghost_value;
 
-constexpr int kMaxNx = 512;  // widest instance: columns per thread = 512 / threads
-constexpr int kSlots = 4;   // window rows (ring)
+constexpr int kNT = 256;       // threads per CTA: thread t owns columns t and t + kNT (one lane pair)
+constexpr int kMaxNx = 2 * kNT;  // widest instance
+constexpr int kSlots = 4;        // window rows (ring)
+constexpr int kWP = kNT + 2;     // paired window entries e = -1 .. kNT at index e + 1
 
 // Per-instance block: the node-function fields (same names as the fused
 // kernel's) and the batch bookkeeping.
@@ -90,21 +98,37 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   return v;
 }
 
-__device__ __forceinline__ void cp16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Test an mbarrier phase; a thread that finds it incomplete is suspended for
+// up to ~0.5 ms (the suspend-time hint) or until the phase completes.
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(500000u)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: false after limit ns without completion.
+__device__ bool mbar_wait(unsigned bar, unsigned parity, unsigned long long limit) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (gtimer() - t0 > limit) return false;
+  }
+}
+
+// One-dimensional bulk copy global -> shared, completion counted in bytes on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
                : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void cp_wait_dyn(int pending) {
-  // pending = stages - 3 in [0, 3]
-  if (pending <= 0) cp_wait<0>();
-  else if (pending == 1) cp_wait<1>();
-  else if (pending == 2) cp_wait<2>();
-  else cp_wait<3>();
 }
 
 // Bounded wait until *p >= target.  False if the batch aborted or the wait ran out.
@@ -119,124 +143,165 @@ __device__ bool wait_ge(const unsigned *p, unsigned target, const int *abort, un
   }
 }
 
+// Shared memory of a CTA (dynamic part, 128-byte aligned base).
+struct Smem {
+  float *stage;              // [S][9][nxs]: rows loaded by bulk copies
+  float2 *wpsi, *wsq;        // [kSlots][kWP]: psi and psi^2 in lane pairs (entry e = columns e, e + kNT)
+  float *wrho;               // [nxs + 2]: boundary-row densities, column c at c + 1 (periodic copies at 0, nx + 1)
+  unsigned long long *bars;  // [S]: one mbarrier per stage
+};
+
+// Row loads of the CTA: count k goes to ring slot k % S with mbarrier phase (k / S) & 1.
+struct Ring {
+  unsigned issued, consumed;
+};
+
 // One item of one step: stream virtual rows y0-1 .. y1 (halo and solid rows
-// included), fill the window, collide rows y0 .. y1-1 into dst.  Thread t owns
-// columns t, t + NT, ... (CPT of them); their densities stay in registers for
-// the collision and the ghost rows, and only the boundary rows' densities (the
-// ghost rule needs their x neighbours) go to shared memory.
-template <bool UNIT, int NT, int CPT>
-__device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__ src, float *__restrict__ dst,
-                      float *stage, float2 *win, float *wrho, int nxs, int S, bool &bad) {
+// included), fill the window, collide rows y0 .. y1-1 into dst.  Rows come in
+// by bulk copies that one thread issues (9 per row, one per plane) into a ring
+// of S stages; a stage is read when its row arrives (rho) and again when the
+// row is collided one iteration later, then refilled.
+// Returns false if a wait on a row ran out (the CTA then aborts).
+template <bool UNIT>
+__device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__ src, float *__restrict__ dst,
+                      const Smem &M, int nxs, int S, Ring &rg, unsigned long long wait_ns, bool &bad) {
   const int tid = threadIdx.x;
-  const int nx = P.nx, ny = P.ny, nx4 = nx >> 2;
+  const int nx = P.nx, ny = P.ny;
   const size_t n = (size_t)nx * ny;
-  const int wn = nxs + 4;  // window row: column c at c + 2
   const int R = it.y1 - it.y0 + 2;
   const bool geo = P.wetting == LBM_WET_GEOMETRIC;
-  const int stage_floats = 9 * nxs;
+  const unsigned row_bytes = (unsigned)nx * 4u;
+  const int c0 = tid, c1 = tid + kNT;
+  const bool act0 = c0 < nx, act1 = c1 < nx;  // act1 implies act0
 
-  // 16-byte chunk q = tid + m NT of a row's 9 nx/4 chunks: plane a, chunk c4
-  // (the split is the same for every row, so it is advanced, not divided)
-  const int a0 = tid / nx4, c40 = tid - a0 * nx4;
-  auto issue = [&](int j) {
-    const int v = it.y0 - 1 + j;
-    if (v <= 0 || v >= ny - 1) return;  // solid rows are not loaded
-    float *st = stage + (size_t)(j % S) * stage_floats;
-    const float *row = src + (size_t)v * nx;
-    int a = a0, c4 = c40;
-    for (int q = tid; q < 9 * nx4; q += NT) {
-      cp16(st + a * nxs + 4 * c4, row + (unsigned)a * (unsigned)n + 4 * c4);
-      c4 += NT;
-      while (c4 >= nx4) {
-        c4 -= nx4;
-        ++a;
-      }
+  int jn = 0;  // next row to load (meaningful in thread 0 only)
+  // a stage stays in use until its row is collided (read in the iteration the
+  // row arrives and in the next one): rows consumed before the previous
+  // iteration are released
+  unsigned released = rg.consumed, start_prev = rg.consumed;
+  auto issue = [&]() {
+    // after the generic-proxy reads of the slots being refilled
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    while (jn < R && rg.issued - released < (unsigned)S) {
+      const int v = it.y0 - 1 + jn;
+      ++jn;
+      if (v <= 0 || v >= ny - 1) continue;  // solid rows are not loaded
+      const int s = (int)(rg.issued % (unsigned)S);
+      const unsigned bar = smem_u32(&M.bars[s]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(9u * row_bytes)
+                   : "memory");
+      float *st = M.stage + (size_t)s * 9 * nxs;
+      const float *row = src + (size_t)v * nx;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) bulk_g2s(smem_u32(st + a * nxs), row + a * n, row_bytes, bar);
+      ++rg.issued;
     }
   };
-  for (int j = 0; j < S - 2; ++j) {
-    if (j < R) issue(j);
-    cp_commit();
-  }
+  if (tid == 0) issue();
 
-  float rc[CPT], rp[CPT], rp2[CPT];  // densities of rows v, v-1, v-2 at the owned columns
-#pragma unroll
-  for (int k = 0; k < CPT; ++k) rc[k] = rp[k] = rp2[k] = 0.0f;
+  // (psi, psi^2) of column c into a window row pair: lane 0 of entry c and/or
+  // lane 1 of entry c - kNT; columns nx-1 and 0 also fill the periodic
+  // entries -1 and nx
+  auto put1 = [&](float2 *ps, float2 *sq, int c, float p, float q) {
+    if (c <= kNT) {
+      ps[c + 1].x = p;
+      sq[c + 1].x = q;
+    }
+    if (c >= kNT - 1) {
+      ps[c - kNT + 1].y = p;
+      sq[c - kNT + 1].y = q;
+    }
+  };
+  auto put = [&](float2 *ps, float2 *sq, int c, float p, float q) {
+    put1(ps, sq, c, p, q);
+    if (c == nx - 1) put1(ps, sq, -1, p, q);
+    if (c == 0) put1(ps, sq, nx, p, q);
+  };
+  auto putr = [&](int c, float r) {
+    M.wrho[c + 1] = r;
+    if (c == nx - 1) M.wrho[0] = r;
+    if (c == 0) M.wrho[nx + 1] = r;
+  };
 
-  for (int j = 0; j < R; ++j) {
+  float2 rc = make_float2(0.0f, 0.0f), rp = rc, rp2 = rc;  // densities of rows v, v-1, v-2 (own columns)
+  bool ok = true;
+  int slot_prev = 0;  // stage of the row loaded in the previous iteration
+
+  auto body = [&](int j) {
     const int v = it.y0 - 1 + j;
-    cp_wait_dyn(S - 3);
-    __syncthreads();  // row j staged by every thread; row j-2's stage and window slot j-4 are free
-    if (j + S - 2 < R) issue(j + S - 2);
-    cp_commit();
-
-    float2 *wcur = win + (size_t)(j & 3) * wn;
+    const unsigned start = rg.consumed;
+    int slot = slot_prev;
+    float2 *pcur = M.wpsi + (size_t)(j & 3) * kWP, *qcur = M.wsq + (size_t)(j & 3) * kWP;
     const bool solid = v == 0 || v == ny - 1;
     if (!solid) {
-      const float *st = stage + (size_t)(j % S) * stage_floats;
+      const int s = (int)(rg.consumed % (unsigned)S);
+      slot = s;
+      const unsigned ph = (rg.consumed / (unsigned)S) & 1u;
+      if (!mbar_wait(smem_u32(&M.bars[s]), ph, wait_ns)) ok = false;
+      ++rg.consumed;
+      const float *st = M.stage + (size_t)s * 9 * nxs;
       const bool brow = v == 1 || v == ny - 2;  // boundary row: the ghost rule reads its neighbours
+      if (act0) {
+        const float *q0 = st + c0, *q1 = st + (act1 ? c1 : c0);
+        float2 fin[9];
 #pragma unroll
-      for (int k = 0; k < CPT; ++k) {
-        const int c = tid + k * NT;
-        if (c < nx) {
-          const float *q = st + c;
-          const float r = (((q[0] + q[nxs]) + (q[2 * nxs] + q[3 * nxs])) +
-                           ((q[4 * nxs] + q[5 * nxs]) + (q[6 * nxs] + q[7 * nxs]))) +
-                          q[8 * nxs];
-          const float4 e = eos_node(P, r);
-          const float2 pe = make_float2(e.y, e.z);
-          rc[k] = r;
-          wcur[c + 2] = pe;
-          if (c == nx - 1) wcur[1] = pe;
-          if (c == 0) wcur[nx + 2] = pe;
-          if (brow) {
-            wrho[c + 2] = r;
-            if (c == nx - 1) wrho[1] = r;
-            if (c == 0) wrho[nx + 2] = r;
-          }
-          bad |= !(r > 0.0f) || r > P.rho_max;
+        for (int a = 0; a < 9; ++a) fin[a] = make_float2(q0[a * nxs], q1[a * nxs]);
+        const float2 r = add2(add2(add2(add2(fin[0], fin[1]), add2(fin[2], fin[3])),
+                                   add2(add2(fin[4], fin[5]), add2(fin[6], fin[7]))),
+                              fin[8]);
+        rc = r;
+        const float4 e0 = eos_node(P, r.x);
+        put(pcur, qcur, c0, e0.y, e0.z);
+        if (brow) putr(c0, r.x);
+        bad |= !(r.x > 0.0f) || r.x > P.rho_max;
+        if (act1) {
+          const float4 e1 = eos_node(P, r.y);
+          put(pcur, qcur, c1, e1.y, e1.z);
+          if (brow) putr(c1, r.y);
+          bad |= !(r.y > 0.0f) || r.y > P.rho_max;
         }
       }
       // bottom ghost row (Eqs. 19-21) once rows 1 and 2 are in: row 1's
       // densities in wrho (written last iteration), row 2's in registers
       if (geo && it.y0 == 1 && v == 2) {
-        float2 *gw = win + (size_t)((j - 2) & 3) * wn;
-#pragma unroll
-        for (int k = 0; k < CPT; ++k) {
-          const int c = tid + k * NT;
-          if (c < nx) {
-            const float4 e = ghost_value(P, wrho[c + 1], wrho[c + 2], wrho[c + 3], rc[k], c, 0);
-            const float2 pe = make_float2(e.y, e.z);
-            gw[c + 2] = pe;
-            if (c == nx - 1) gw[1] = pe;
-            if (c == 0) gw[nx + 2] = pe;
-          }
+        float2 *gp = M.wpsi + (size_t)((j - 2) & 3) * kWP, *gq = M.wsq + (size_t)((j - 2) & 3) * kWP;
+        if (act0) {
+          const float4 e = ghost_value(P, M.wrho[c0], M.wrho[c0 + 1], M.wrho[c0 + 2], rc.x, c0, 0);
+          put(gp, gq, c0, e.y, e.z);
+        }
+        if (act1) {
+          const float4 e = ghost_value(P, M.wrho[c1], M.wrho[c1 + 1], M.wrho[c1 + 2], rc.y, c1, 0);
+          put(gp, gq, c1, e.y, e.z);
         }
       }
     } else if (!geo || v == ny - 1) {
       // Martys-Chen: solid rows carry psi = U = 0.  Geometric: the top ghost
       // row from rows ny-2 (wrho) and ny-3 (registers); the bottom one is filled at v == 2.
-#pragma unroll
-      for (int k = 0; k < CPT; ++k) {
-        const int c = tid + k * NT;
-        if (c < nx) {
-          float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          if (geo) e = ghost_value(P, wrho[c + 1], wrho[c + 2], wrho[c + 3], rp2[k], c, 1);
-          const float2 pe = make_float2(e.y, e.z);
-          wcur[c + 2] = pe;
-          if (c == nx - 1) wcur[1] = pe;
-          if (c == 0) wcur[nx + 2] = pe;
-        }
+      if (act0) {
+        float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (geo) e = ghost_value(P, M.wrho[c0], M.wrho[c0 + 1], M.wrho[c0 + 2], rp2.x, c0, 1);
+        put(pcur, qcur, c0, e.y, e.z);
+      }
+      if (act1) {
+        float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (geo) e = ghost_value(P, M.wrho[c1], M.wrho[c1 + 1], M.wrho[c1 + 2], rp2.y, c1, 1);
+        put(pcur, qcur, c1, e.y, e.z);
       }
     }
-    __syncthreads();  // window row j complete
+    // window row j complete; row j's stage read (refillable); a row wait
+    // that ran out in any thread ends the item in all of them
+    ok = !__syncthreads_or(!ok);
+    if (!ok) return;
+    released = start_prev;  // every row before row j-1 is collided
+    start_prev = start;
+    if (tid == 0) issue();
 
-    // ---- collide row v-1 (its populations are in the stage of row j-1) ----
+    // ---- collide row v-1 (its populations are in the stage of the previous iteration) ----
     const int y = v - 1;
-    if (j >= 1 && y >= it.y0 && y < it.y1) {
-      const float2 *wm = win + (size_t)((j - 2) & 3) * wn;
-      const float2 *w0 = win + (size_t)((j - 1) & 3) * wn;
-      const float2 *wp = wcur;
-      const float *st = stage + (size_t)((j - 1) % S) * stage_floats;
+    if (act0 && j >= 1 && y >= it.y0 && y < it.y1) {
+      const float2 *pm = M.wpsi + (size_t)((j - 2) & 3) * kWP, *qm = M.wsq + (size_t)((j - 2) & 3) * kWP;
+      const float2 *p0 = M.wpsi + (size_t)((j - 1) & 3) * kWP, *q0 = M.wsq + (size_t)((j - 1) & 3) * kWP;
+      const float2 *pp = pcur, *qp = qcur;
       const bool wall_dn = y == 1, wall_up = y == ny - 2;
       // warp-uniform plane pointers; each store adds one 32-bit element offset
       // (9 nx ny < 2^31 is checked at creation)
@@ -244,72 +309,92 @@ __device__ void sweep(const BInst &P, const BItem &it, const float *__restrict__
       float *const o0 = dst, *const o1 = o0 + un, *const o2 = o1 + un, *const o3 = o2 + un, *const o4 = o3 + un;
       float *const o5 = o4 + un, *const o6 = o5 + un, *const o7 = o6 + un, *const o8 = o7 + un;
       const unsigned ry = (unsigned)y * nx, rym = ry - nx, ryp = ry + nx;
-#pragma unroll
-      for (int k = 0; k < CPT; ++k) {
-        const int c = tid + k * NT;
-        if (c >= nx) break;
-        const int i0 = c + 2;
-        float2 nb[9];
-        nb[0] = w0[i0];
-        nb[1] = w0[i0 + 1];
-        nb[2] = wp[i0];
-        nb[3] = w0[i0 - 1];
-        nb[4] = wm[i0];
-        nb[5] = wp[i0 + 1];
-        nb[6] = wp[i0 - 1];
-        nb[7] = wm[i0 - 1];
-        nb[8] = wm[i0 + 1];
-        float f[9], fs[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) f[a] = st[a * nxs + c];
-        collide_node<UNIT>(P, f, nb, rp[k], y, fs);
-        const unsigned x = c;
-        const unsigned xm = c == 0 ? nx - 1 : c - 1, xp = c == nx - 1 ? 0 : c + 1;
-        o0[ry + x] = fs[0];
-        o1[ry + xp] = fs[1];
-        o3[ry + xm] = fs[3];
+      auto push = [&](unsigned x, float f0, float f1, float f2, float f3, float f4, float f5, float f6, float f7,
+                      float f8) {
+        const unsigned xm = x == 0 ? nx - 1 : x - 1, xp = x == (unsigned)nx - 1 ? 0 : x + 1;
+        o0[ry + x] = f0;
+        o1[ry + xp] = f1;
+        o3[ry + xm] = f3;
         if (wall_up) {
-          o4[ry + x] = fs[2];
-          o7[ry + x] = fs[5];
-          o8[ry + x] = fs[6];
+          o4[ry + x] = f2;
+          o7[ry + x] = f5;
+          o8[ry + x] = f6;
         } else {
-          o2[ryp + x] = fs[2];
-          o5[ryp + xp] = fs[5];
-          o6[ryp + xm] = fs[6];
+          o2[ryp + x] = f2;
+          o5[ryp + xp] = f5;
+          o6[ryp + xm] = f6;
         }
         if (wall_dn) {
-          o2[ry + x] = fs[4];
-          o5[ry + x] = fs[7];
-          o6[ry + x] = fs[8];
+          o2[ry + x] = f4;
+          o5[ry + x] = f7;
+          o6[ry + x] = f8;
         } else {
-          o4[rym + x] = fs[4];
-          o7[rym + xm] = fs[7];
-          o8[rym + xp] = fs[8];
+          o4[rym + x] = f4;
+          o7[rym + xm] = f7;
+          o8[rym + xp] = f8;
         }
-      }
-    }
+      };
+      const int i = tid + 1;
+      float2 pn[9], qn[9], fs[9];
+      pn[0] = p0[i];
+      qn[0] = q0[i];
+      pn[1] = p0[i + 1];
+      qn[1] = q0[i + 1];
+      pn[2] = pp[i];
+      qn[2] = qp[i];
+      pn[3] = p0[i - 1];
+      qn[3] = q0[i - 1];
+      pn[4] = pm[i];
+      qn[4] = qm[i];
+      pn[5] = pp[i + 1];
+      qn[5] = qp[i + 1];
+      pn[6] = pp[i - 1];
+      qn[6] = qp[i - 1];
+      pn[7] = pm[i - 1];
+      qn[7] = qm[i - 1];
+      pn[8] = pm[i + 1];
+      qn[8] = qm[i + 1];
+      const float *sp = M.stage + (size_t)slot_prev * 9 * nxs;
+      const float *fa = sp + c0, *fb = sp + (act1 ? c1 : c0);
+      float2 fcol[9];
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-      rp2[k] = rp[k];
-      rp[k] = rc[k];
+      for (int a = 0; a < 9; ++a) fcol[a] = make_float2(fa[a * nxs], fb[a * nxs]);
+      collide_node2<UNIT>(P, fcol, pn, qn, rp, y, fs);
+      push((unsigned)c0, fs[0].x, fs[1].x, fs[2].x, fs[3].x, fs[4].x, fs[5].x, fs[6].x, fs[7].x, fs[8].x);
+      if (act1) push((unsigned)c1, fs[0].y, fs[1].y, fs[2].y, fs[3].y, fs[4].y, fs[5].y, fs[6].y, fs[7].y, fs[8].y);
     }
-  }
-  cp_wait<0>();  // no copy of this item stays in flight into the next one's stages
+    rp2 = rp;
+    rp = rc;
+    slot_prev = slot;
+  };
+  for (int j = 0; j < R && ok; ++j) body(j);
+  return ok;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 5) k_batch(BatchArgs A) {
-  constexpr int CPT = kMaxNx / NT;
-  extern __shared__ __align__(16) float smem_f[];
+__global__ void __launch_bounds__(kNT, 3) k_batch(BatchArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ BInst sP;
   __shared__ BItem s_it;
-  __shared__ int s_go, s_skip, s_bad, s_step, s_idx;
+  __shared__ int s_go, s_skip, s_bad, s_step, s_idx, s_timeout;
+  unsigned char *base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int S = A.stages, nxs = A.nxs;
-  float *stage = smem_f;
-  float2 *win = (float2 *)(stage + (size_t)S * 9 * nxs);
-  float *wrho = (float *)(win + (size_t)kSlots * (nxs + 4));
+  Smem M;
+  M.stage = (float *)base;
+  M.wpsi = (float2 *)(M.stage + (size_t)S * 9 * nxs);
+  M.wsq = M.wpsi + kSlots * kWP;
+  M.wrho = (float *)(M.wsq + kSlots * kWP);
+  M.bars = (unsigned long long *)(M.wrho + ((nxs + 2 + 1) & ~1));
   const int tid = threadIdx.x;
   const unsigned total = (unsigned)A.steps * (unsigned)A.nitems;
+  if (tid == 0) {
+    s_timeout = 0;
+    for (int s = 0; s < S; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&M.bars[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  Ring rg{0u, 0u};
 
   for (;;) {
     if (tid == 0) {
@@ -330,6 +415,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 5) k_batch(BatchArgs A) {
           go = 0;
         }
         if (go) {
+          // the rows about to be loaded by the bulk (asynchronous-proxy) copies
+          // were written by generic stores of this and other CTAs before the
+          // barrier just acquired
+          asm volatile("fence.proxy.async.global;" ::: "memory");
           sP = *gp;
           s_it = it;
           s_step = s;
@@ -342,18 +431,25 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 5) k_batch(BatchArgs A) {
       s_go = go;
     }
     __syncthreads();
-    if (!s_go) return;
+    if (!s_go) break;
     const BItem it = s_it;
     const int par = A.cur[it.inst] ^ ((A.phase + s_step) & 1);
     bool bad = false;
     if (!s_skip) {
-      if (sP.unit)
-        sweep<true, NT, CPT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, wrho, nxs, S, bad);
-      else
-        sweep<false, NT, CPT>(sP, it, sP.f[par], sP.f[par ^ 1], stage, win, wrho, nxs, S, bad);
+      bool ok = sP.unit ? sweep<true>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad)
+                        : sweep<false>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad);
+      if (!ok) s_timeout = 1;
     }
     if (bad) s_bad = 1;
     __syncthreads();  // every store of the item issued; shared state free for the next entry
+    if (s_timeout) {
+      if (tid == 0) {
+        atomicOr(A.iflag + it.inst, 2);
+        atomicOr(sP.flag + 1, 1);
+        atomicExch(A.abort, 1);
+      }
+      break;
+    }
     if (tid == 0) {
       if (s_bad) {
         atomicOr(A.iflag + it.inst, 1);
@@ -365,13 +461,18 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 5) k_batch(BatchArgs A) {
       }
     }
   }
+  // no bulk copy may still be writing into this CTA's shared memory when it
+  // exits (only possible after a timeout): wait for them, bounded
+  if (tid == 0)
+    for (unsigned k = rg.consumed; k < rg.issued; ++k)
+      mbar_wait(smem_u32(&M.bars[k % (unsigned)S]), (k / (unsigned)S) & 1u, A.wait_ns);
 }
 
-const void *kernel_ptr(int nt) { return nt == 256 ? (const void *)k_batch<256> : (const void *)k_batch<128>; }
+const void *kernel_ptr() { return (const void *)k_batch; }
 
 size_t smem_bytes(int nxs, int stages) {
-  return (size_t)stages * 9 * nxs * sizeof(float) + (size_t)kSlots * (nxs + 4) * sizeof(float2) +
-         (size_t)(nxs + 4) * sizeof(float);
+  return 128 + (size_t)stages * 9 * nxs * sizeof(float) + (size_t)2 * kSlots * kWP * sizeof(float2) +
+         (size_t)((nxs + 2 + 1) & ~1) * sizeof(float) + (size_t)stages * 8;
 }
 
 int size_class(int nx) { return nx <= 128 ? 0 : nx <= 256 ? 1 : nx <= 384 ? 2 : 3; }
@@ -431,8 +532,8 @@ int resolve_config(const lbm_batch *B, const lbm_batch_config *in, lbm_batch_con
   lbm_batch_config c = *in;
   int nxmax = 0;
   for (int i = 0; i < B->n; ++i) nxmax = std::max(nxmax, B->ctx[i]->nx);
-  if (c.threads == 0) c.threads = 256;
-  if (c.threads != 128 && c.threads != 256) return LBM_EINVAL;
+  if (c.threads == 0) c.threads = kNT;
+  if (c.threads != kNT) return LBM_EINVAL;
   if (nxmax > kMaxNx) return LBM_EUNSUPPORTED;
   if (c.stages == 0) c.stages = 4;
   if (c.stages < 3 || c.stages > 6) return LBM_EINVAL;
@@ -471,7 +572,7 @@ int plan(lbm_batch *B) {
   if ((long long)nitems * c.steps_per_launch >= (1LL << 31)) return LBM_EUNSUPPORTED;
   B->nxs = (nxmax + 3) & ~3;
   B->smem = (int)smem_bytes(B->nxs, c.stages);
-  const void *kern = kernel_ptr(c.threads);
+  const void *kern = kernel_ptr();
   int dev = 0, occ = 0, optin = 0;
   BCK(cudaGetDevice(&dev));
   // the attribute is per kernel, not per batch: allow the device maximum so
@@ -483,7 +584,7 @@ int plan(lbm_batch *B) {
   if (B->smem > dyn_max) return LBM_EUNSUPPORTED;
   BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
   BCK(cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, dev));
-  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, c.threads, B->smem));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kNT, B->smem));
   if (occ < 1) return LBM_EUNSUPPORTED;
   if (c.ctas_per_sm > 0 && c.ctas_per_sm < occ) occ = c.ctas_per_sm;
   B->occ = occ;
@@ -522,7 +623,7 @@ int launch(lbm_batch *B, int steps, int phase) {
   BCK(cudaMemsetAsync(B->d_bar, 0, (size_t)(B->n + 1) * sizeof(unsigned), B->stream));
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(B->grid);
-  lc.blockDim = dim3(B->cfg.threads);
+  lc.blockDim = dim3(kNT);
   lc.dynamicSmemBytes = B->smem;
   lc.stream = B->stream;
   cudaLaunchAttribute at[1];
@@ -530,7 +631,7 @@ int launch(lbm_batch *B, int steps, int phase) {
   at[0].val.cooperative = 1;
   lc.attrs = at;
   lc.numAttrs = steps > 1 ? 1 : 0;
-  cudaError_t e = B->cfg.threads == 256 ? cudaLaunchKernelEx(&lc, k_batch<256>, A) : cudaLaunchKernelEx(&lc, k_batch<128>, A);
+  cudaError_t e = cudaLaunchKernelEx(&lc, k_batch, A);
   BCK(e);
   ++B->launches;
   return LBM_OK;
