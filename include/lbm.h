@@ -101,6 +101,10 @@ typedef struct lbm_params {
                         with p(rho) = rho/3 (psi^2 >= 0 below it) */
   double rho_ghost_max; /* upper clamp of the Eqs. 19-21 ghost densities
                         (lower clamp 0); 0 means rho_max */
+  int graph_steps;   /* lbm_step replays this many steps (rounded up to even) as
+                        one captured CUDA graph while at least that many remain,
+                        when the context has a non-NULL stream; 0 = one launch
+                        sequence per step.  Results are the same either way. */
 } lbm_params;
 
 /* Values of a created context (for bookkeeping and tests). */
@@ -117,7 +121,7 @@ typedef struct lbm_ctx lbm_ctx;
 const char *lbm_strerror(int status);
 
 /* Defaults of Sec. 3.1: A = -0.6, kappa = 0.5, G_w = 0, n_iter = 4, geometric
- * wetting, FP32, AUTO kernel, all rates 1/tau, check_every = 100,
+ * wetting, FP32, AUTO kernel, all rates 1/tau, check_every = 100, graph_steps = 64,
  * rho_mid = rho_max = 0 (derived).  LBM_EINVAL if p is NULL. */
 int lbm_params_default(lbm_params *p);
 

@@ -55,6 +55,11 @@ struct lbm_tape {
   double *gpart;                 // [2 walls][4][nx]: ghost-rule partials
   double *dtheta;                // [2][nx]
   double *red;                   // reduction output
+  // captured graphs (contexts with a non-NULL stream): the recorded forward of
+  // one full segment per starting array, and the replay + reverse sweep of one
+  // full segment per starting adjoint buffer
+  cudaGraphExec_t fwd_graph[2], bwd_graph[2];
+  unsigned long long fwd_launches, bwd_launches;  // kernels per replay
 };
 
 namespace {
@@ -413,6 +418,45 @@ int reverse_step(lbm_ctx *C, lbm_tape *T, const void *f, int lin) {
   return LBM_OK;
 }
 
+// Capture the work that fn() enqueues on the context stream into *out; the
+// kernels it launches are counted into *launches (not into the context).
+template <typename Fn>
+int capture(lbm_ctx *C, cudaGraphExec_t *out, unsigned long long *launches, Fn fn) {
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  const unsigned long long l0 = C->launches;
+  int st = fn();
+  *launches = C->launches - l0;
+  C->launches = l0;
+  cudaError_t e = cudaStreamEndCapture(C->stream, &graph);
+  if (st == LBM_OK && e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (st == LBM_OK && e != cudaSuccess) st = LBM_ECUDA;
+  if (st != LBM_OK) {
+    cudaGetLastError();
+    *out = nullptr;
+  }
+  return st;
+}
+
+// Replay of a segment from seg[0] (len states) and its reverse sweep, adjoint
+// starting in lam[lin]; returns the status and leaves the final buffer in *lin.
+template <typename R>
+int segment_reverse(lbm_ctx *C, lbm_tape *T, int len, int *lin) {
+  char *seg = (char *)T->seg;
+  int st = LBM_OK;
+  for (int k = 0; k + 1 < len && st == LBM_OK; ++k)
+    st = ref_step(C, seg + (size_t)k * T->state_bytes, seg + (size_t)(k + 1) * T->state_bytes);
+  for (int k = len - 1; k >= 0 && st == LBM_OK; --k) {
+    st = reverse_step<R>(C, T, seg + (size_t)k * T->state_bytes, *lin);
+    *lin ^= 1;
+  }
+  return st;
+}
+
 template <typename R>
 int backward(lbm_ctx *C, lbm_tape *T, const double *dl_drho, double *dl_dtheta, double *dl_dT, double *dl_df0) {
   const size_t n = (size_t)C->nx * C->ny;
@@ -438,16 +482,28 @@ int backward(lbm_ctx *C, lbm_tape *T, const double *dl_drho, double *dl_dtheta, 
   for (int sgi = T->nseg - 1; sgi >= 0 && st == LBM_OK; --sgi) {
     const int s0 = sgi * T->every, len = (sgi == T->nseg - 1) ? T->nsteps - s0 : T->every;
     // replay the segment: states s0 .. s0 + len - 1 into the segment buffer
-    char *seg = (char *)T->seg;
-    if (cudaMemcpyAsync(seg, T->ckpt[sgi], T->state_bytes, cudaMemcpyDeviceToDevice, C->stream) != cudaSuccess) {
+    if (cudaMemcpyAsync(T->seg, T->ckpt[sgi], T->state_bytes, cudaMemcpyDeviceToDevice, C->stream) != cudaSuccess) {
       st = LBM_ECUDA;
       break;
     }
-    for (int k = 0; k + 1 < len && st == LBM_OK; ++k)
-      st = ref_step(C, seg + (size_t)k * T->state_bytes, seg + (size_t)(k + 1) * T->state_bytes);
-    for (int k = len - 1; k >= 0 && st == LBM_OK; --k) {
-      st = reverse_step<R>(C, T, seg + (size_t)k * T->state_bytes, lin);
-      lin ^= 1;
+    if (C->stream && len == T->every) {
+      const int l0 = lin;
+      if (!T->bwd_graph[l0]) {
+        st = capture(C, &T->bwd_graph[l0], &T->bwd_launches, [&]() {
+          int l = l0;
+          return segment_reverse<R>(C, T, len, &l);
+        });
+        if (st) break;
+      }
+      if (cudaGraphLaunch(T->bwd_graph[l0], C->stream) != cudaSuccess) {
+        cudaGetLastError();
+        st = LBM_ECUDA;
+        break;
+      }
+      C->launches += T->bwd_launches;
+      lin ^= len & 1;
+    } else {
+      st = segment_reverse<R>(C, T, len, &lin);
     }
   }
   if (st == LBM_OK) {
@@ -500,6 +556,10 @@ void lbm_adjoint_free_tape(lbm_ctx *C) {
   cudaFree(T->gpart);
   cudaFree(T->dtheta);
   cudaFree(T->red);
+  for (int p = 0; p < 2; ++p) {
+    if (T->fwd_graph[p]) cudaGraphExecDestroy(T->fwd_graph[p]);
+    if (T->bwd_graph[p]) cudaGraphExecDestroy(T->bwd_graph[p]);
+  }
   cudaGetLastError();
   delete T;
   C->tape = nullptr;
@@ -541,22 +601,40 @@ int lbm_adjoint_record(lbm_ctx *C, int nsteps, int checkpoint_every) {
     return LBM_ENOMEM;
   }
   // run the steps with the reference kernels, keeping the state at each segment start
-  for (int s = 0; s < nsteps; ++s) {
-    if (s % T->every == 0 &&
-        cudaMemcpyAsync(T->ckpt[s / T->every], C->f[C->cur], T->state_bytes, cudaMemcpyDeviceToDevice,
-                        C->stream) != cudaSuccess) {
+  for (int sg = 0; sg < T->nseg; ++sg) {
+    const int len = sg == T->nseg - 1 ? nsteps - sg * T->every : T->every;
+    int st = LBM_OK;
+    if (cudaMemcpyAsync(T->ckpt[sg], C->f[C->cur], T->state_bytes, cudaMemcpyDeviceToDevice, C->stream) !=
+        cudaSuccess) {
       cudaGetLastError();
-      lbm_adjoint_free_tape(C);
-      return LBM_ECUDA;
+      st = LBM_ECUDA;
     }
-    int st = ref_step(C, C->f[C->cur], C->f[C->cur ^ 1]);
+    auto steps = [&](int count, int cur) {
+      int r = LBM_OK;
+      for (int k = 0; k < count && r == LBM_OK; ++k) r = ref_step(C, C->f[cur ^ (k & 1)], C->f[cur ^ (k & 1) ^ 1]);
+      return r;
+    };
+    if (st == LBM_OK && C->stream && len == T->every) {
+      const int p = C->cur;
+      if (!T->fwd_graph[p]) st = capture(C, &T->fwd_graph[p], &T->fwd_launches, [&]() { return steps(len, p); });
+      if (st == LBM_OK) {
+        if (cudaGraphLaunch(T->fwd_graph[p], C->stream) != cudaSuccess) {
+          cudaGetLastError();
+          st = LBM_ECUDA;
+        } else {
+          C->launches += T->fwd_launches;
+        }
+      }
+    } else if (st == LBM_OK) {
+      st = steps(len, C->cur);
+    }
     if (st) {
       lbm_adjoint_free_tape(C);
       C->status = st;
       return st;
     }
-    C->cur ^= 1;
-    C->steps++;
+    C->cur ^= len & 1;
+    C->steps += len;
   }
   if (cudaStreamSynchronize(C->stream) != cudaSuccess) {
     cudaGetLastError();

@@ -232,6 +232,48 @@ int read_flags(lbm_ctx *C) {
   return C->status;
 }
 
+// One step from array src to src ^ 1, with the kernel chosen at creation.
+cudaError_t launch_step(lbm_ctx *C, int src, unsigned long long *launches) {
+  const int dst = src ^ 1;
+  if (C->kernel_in_use == LBM_KERNEL_FUSED) return lbm_fused_step(C, src, launches);
+  cudaError_t e = lbm_ref_fields(C, C->f[src], C->d_fields, launches);
+  if (e == cudaSuccess) e = lbm_ref_ghost(C, C->d_fields, launches);
+  if (e == cudaSuccess) e = lbm_ref_collide(C, C->f[src], C->f[dst], C->d_fields, launches);
+  return e;
+}
+
+int launches_per_step(const lbm_ctx *C) { return C->kernel_in_use == LBM_KERNEL_FUSED ? 1 : 3; }
+
+// Steps per captured graph (even), or 0 when graphs are off or impossible
+// (the legacy default stream cannot be captured).
+int graph_steps(const lbm_ctx *C) {
+  int g = C->params.graph_steps;
+  if (g <= 0 || !C->stream) return 0;
+  return g + (g & 1);
+}
+
+// Capture G steps starting from array C->cur into an executable graph.
+int capture_steps(lbm_ctx *C, int G, cudaGraphExec_t *out) {
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  unsigned long long dummy = 0;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < G && e == cudaSuccess; ++k) e = launch_step(C, C->cur ^ (k & 1), &dummy);
+  cudaError_t e2 = cudaStreamEndCapture(C->stream, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return LBM_ECUDA;
+  }
+  return LBM_OK;
+}
+
 int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const double *theta,
                 const uint8_t *wall_mask, const lbm_params *params, void *stream, void *state, size_t state_bytes,
                 lbm_ctx **out) {
@@ -244,7 +286,7 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
   if (P.n_iter < 0 || P.n_iter > 64) return LBM_EINVAL;
   if (P.wetting != LBM_WET_GEOMETRIC && P.wetting != LBM_WET_MARTYS_CHEN) return LBM_EINVAL;
   if (P.kernel < LBM_KERNEL_AUTO || P.kernel > LBM_KERNEL_FUSED) return LBM_EINVAL;
-  if (P.check_every < 0) return LBM_EINVAL;
+  if (P.check_every < 0 || P.graph_steps < 0) return LBM_EINVAL;
   if ((size_t)nx * (size_t)ny > ((size_t)1 << 31) / 9) return LBM_EUNSUPPORTED;
   // walls: none, or exactly the two full rows y = 0 and y = ny - 1
   int walls = 0;
@@ -418,6 +460,7 @@ int lbm_params_default(lbm_params *p) {
   p->precision = 32;
   p->kernel = LBM_KERNEL_AUTO;
   p->check_every = 100;
+  p->graph_steps = 64;
   return LBM_OK;
 }
 
@@ -493,16 +536,31 @@ int lbm_init_droplets(lbm_ctx *C, int n, const double *xc, const double *radius,
 int lbm_step(lbm_ctx *C, int nsteps) {
   if (!C || nsteps < 0) return LBM_EINVAL;
   if (C->status) return C->status;
-  for (int it = 0; it < nsteps; ++it) {
-    int src = C->cur, dst = src ^ 1;
-    if (C->kernel_in_use == LBM_KERNEL_FUSED) {
-      CK(lbm_fused_step(C, src, &C->launches));
-    } else {
-      CK(lbm_ref_fields(C, C->f[src], C->d_fields, &C->launches));
-      CK(lbm_ref_ghost(C, C->d_fields, &C->launches));
-      CK(lbm_ref_collide(C, C->f[src], C->f[dst], C->d_fields, &C->launches));
+  const int G = graph_steps(C);
+  int it = 0;
+  if (G > 0) {
+    // whole graphs of G (even) steps: each replay starts and ends on the same array
+    while (nsteps - it >= G) {
+      cudaGraphExec_t &g = C->step_graph[C->cur];
+      if (!g) {
+        int st = capture_steps(C, G, &g);
+        if (st) return st;
+      }
+      CK(cudaGraphLaunch(g, C->stream));
+      C->launches += (unsigned long long)G * launches_per_step(C);
+      const long long before = C->steps;
+      C->steps += G;
+      it += G;
+      const int ce = C->params.check_every;
+      if (ce > 0 && C->steps / ce != before / ce) {
+        int st = read_flags(C);
+        if (st) return st;
+      }
     }
-    C->cur = dst;
+  }
+  for (; it < nsteps; ++it) {
+    CK(launch_step(C, C->cur, &C->launches));
+    C->cur ^= 1;
     C->steps++;
     if (C->params.check_every > 0 && C->steps % C->params.check_every == 0) {
       int st = read_flags(C);
@@ -716,6 +774,8 @@ int lbm_sync(lbm_ctx *C) {
 void lbm_destroy(lbm_ctx *C) {
   if (!C) return;
   cudaStreamSynchronize(C->stream);
+  for (int p = 0; p < 2; ++p)
+    if (C->step_graph[p]) cudaGraphExecDestroy(C->step_graph[p]);
   lbm_adjoint_free_tape(C);
   if (C->owns_state && C->state) cudaFree(C->state);
   if (C->d_coef) cudaFree(C->d_coef);

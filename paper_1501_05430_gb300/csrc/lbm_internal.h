@@ -61,6 +61,8 @@ struct lbm_ctx {
   int fused_cols;            // columns per thread of the fused kernel
   int tile_w, tile_blocks, tile_stages, fused_smem;
   unsigned char tmaps[4][128];   // CUtensorMap for f[0], f[1]: main box, halo box
+  // lbm_step graphs: graph_steps steps captured once per starting array
+  cudaGraphExec_t step_graph[2];
 };
 
 // ---- lbm_ref.cu: unfused kernels in the canonical evaluation order --------

@@ -53,7 +53,7 @@ class lbm_params(ctypes.Structure):
                 ("wetting", c_int), ("precision", c_int), ("kernel", c_int),
                 ("s_e", c_double), ("s_eps", c_double), ("s_j", c_double), ("s_q", c_double),
                 ("s_nu", c_double), ("check_every", c_int), ("rho_mid", c_double),
-                ("rho_max", c_double), ("rho_ghost_max", c_double)]
+                ("rho_max", c_double), ("rho_ghost_max", c_double), ("graph_steps", c_int)]
 
 
 class lbm_info(ctypes.Structure):

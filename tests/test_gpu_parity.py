@@ -309,3 +309,43 @@ def test_contexts_with_different_fused_rings_coexist(monkeypatch):
     assert np.array_equal(a.gpu.f(), b.gpu.f())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("kernel", [FUSED, REF])
+def test_graph_replay_equals_direct_launches(kernel):
+    """lbm_step with graphs of 16 steps (on a non-default stream) gives the
+    same bits and counts the same launches as one launch sequence per step."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    w = I.single_droplet(60.0)
+    runs = []
+    for gs in (16, 0):
+        p = Pair(w.nx, w.ny, t_over_tc=w.t_over_tc, tau=w.tau, theta=w.theta, rates=w.rates, eos=w.eos,
+                 precision=32, kernel=kernel, stream=stream)
+        p.gpu.close()
+        p.params.graph_steps = gs
+        g = L.Lbm(w.nx, w.ny, p.geos, p.T, p.tau, theta=p.theta, params=p.params, stream=stream, torch_state=False)
+        g.set_rho(I.droplet_field(w.nx, w.ny, w.droplets, p.rho_v, p.rho_l, w.width))
+        l0 = g.launches()
+        g.step(37)
+        g.step(50)
+        runs.append((g.f(), g.launches() - l0, g.info.steps_done))
+        g.close()
+        p.orc.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1:] == runs[1][1:]
+
+
+def test_graph_replay_reports_instability():
+    import torch
+
+    stream = torch.cuda.Stream()
+    p = Pair(40, 20, precision=32, kernel=FUSED, check_every=32, stream=stream)
+    f = I.random_distributions(I.droplet_field(40, 20, [(20.0, 6.0, 0)], p.rho_v, p.rho_l), 3)
+    f[:, 7, 11] = np.nan
+    p.gpu.set_f(f)
+    with pytest.raises(L.LbmError) as e:
+        p.gpu.step(64)  # one graph of 64 steps, then the check at step 64
+    assert e.value.status == L.LBM_EUNSTABLE
+    p.close()
