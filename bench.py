@@ -16,7 +16,9 @@ deg), 5000 steps -- in FP32 with the fused kernel.
 * roofline: the fused step kernel against the measured HBM copy bandwidth;
   algorithmic bytes = 72 B per fluid node (9 float loads + 9 float stores).
 * cpu_baseline / --impl reference: the FP64 CPU oracle (single thread) on a
-  bounded sample of the same workload.
+  bounded sample of the same workload; --oracle-procs P runs P concurrent
+  single-threaded replicas of that sample (0: one per host core) and reports
+  their aggregate.
 """
 from __future__ import annotations
 
@@ -194,42 +196,87 @@ def cpu_oracle_rate(w, budget_nodes_steps: float, steps_cap: int = 3):
     return nx * (ny - 2) * steps / dt / 1e6, f"{nx}x{ny} crop of the workload, {steps} step(s)", nx, ny, steps
 
 
-def run_reference(args):
-    ws, rank, _ = _dist()
-    if rank != 0:
-        return 0
-    import oracle as O
+def _reference_sample(w, args):
+    """Crop of the workload (both walls kept) sized so that the whole
+    --steps/--warmup run of one oracle process ends in about two minutes."""
+    per_step = 2.5e6 * 100.0 / max(1, args.steps + args.warmup)
+    frac = min(1.0, per_step / (w.nx * (w.ny - 2)))
+    nx = max(64, min(w.nx, int(w.nx * np.sqrt(frac)) // 4 * 4))
+    ny = max(16, min(w.ny, int(w.ny * np.sqrt(frac))))
+    return nx, ny
 
+
+def _reference_replica(job):
+    """One oracle process: build the sample, run the warm-up, wait for the
+    other replicas, then time the steps.  Returns (node-steps, t0, t1, status)
+    with t0/t1 on the host's monotonic clock (shared by all processes)."""
+    size, nx, ny, warmup, steps = job
+    import oracle as O
+    from paper_1501_05430_gb300 import inputs as I
+
+    _SIZE.update(size)
     w = _workload()
     oeos, T, rv, rl = _oracle_setup(O, w)
-    # each step: one oracle step on a crop sized so the whole run ends in ~2 minutes
-    per_step = 2.5e6 * 100.0 / max(1, args.steps + args.warmup)
     rm = O.rho_max(oeos, T, rl)
     inv = 1.0 / w.tau
     r = dict(s_rho=0.0, s_e=w.rates.get("s_e", inv), s_eps=w.rates.get("s_eps", inv), s_j=w.rates.get("s_j", inv),
              s_q=w.rates.get("s_q", inv), s_nu=inv)
-    frac = min(1.0, per_step / (w.nx * (w.ny - 2)))
-    nx = max(64, min(w.nx, int(w.nx * np.sqrt(frac)) // 4 * 4))
-    ny = max(16, min(w.ny, int(w.ny * np.sqrt(frac))))
-    from paper_1501_05430_gb300 import inputs as I
-
     rho = I.droplet_field(w.nx, w.ny, w.droplets, rv, rl, w.width)
     crop = np.ascontiguousarray(rho[:ny, :nx])
     sim = O.Sim(nx, ny, oeos, T, tau=w.tau, theta=np.ascontiguousarray(w.theta[:ny, :nx]), rates=r, rho_max_=rm,
                 A=w.A, kappa=w.kappa)
     sim.set_rho(crop)
-    sim.step(args.warmup)
-    t0 = time.perf_counter()
-    st = sim.step(args.steps)
-    dt = time.perf_counter() - t0
-    value = nx * (ny - 2) * args.steps / dt / 1e6
+    sim.step(warmup)
+    if _REPLICA_BARRIER is not None:
+        _REPLICA_BARRIER.wait()
+    t0 = time.monotonic()
+    st = sim.step(steps)
+    t1 = time.monotonic()
+    sim.close()
+    return nx * (ny - 2) * steps, t0, t1, st
+
+
+_REPLICA_BARRIER = None
+
+
+def _replica_init(barrier):
+    global _REPLICA_BARRIER
+    _REPLICA_BARRIER = barrier
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = _workload()
+    nx, ny = _reference_sample(w, args)
+    procs = max(1, args.oracle_procs)
+    job = (dict(_SIZE), nx, ny, args.warmup, args.steps)
+    if procs == 1:
+        work, t0, t1, st = _reference_replica(job)
+        results = [(work, t0, t1, st)]
+    else:
+        # independent replicas of the same sample in spawned processes, one per
+        # core; the oracle itself stays single-threaded
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(procs)
+        with ctx.Pool(procs, initializer=_replica_init, initargs=(barrier,)) as pool:
+            results = pool.map(_reference_replica, [job] * procs)
+    work = sum(r[0] for r in results)
+    dt = max(r[2] for r in results) - min(r[1] for r in results)
+    st = min(r[3] for r in results)
+    value = work / dt / 1e6
     sample = f"{nx}x{ny} crop of {w.name} (both walls, its droplets and angles), {args.steps} steps"
+    if procs > 1:
+        sample += f", {procs} concurrent single-threaded replicas"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "sample": sample, "oracle_status": st},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": procs, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -507,6 +554,9 @@ def main():
                          "(default: autotune)")
     ap.add_argument("--batch-steps", type=int, default=2000,
                     help="steps of the batched-sweep comparison (0 skips it)")
+    ap.add_argument("--oracle-procs", type=int, default=1,
+                    help="--impl reference: run this many concurrent single-threaded oracle replicas "
+                         "(0 = one per host core) and report their aggregate MLUPS")
     ap.add_argument("--nx", type=int, default=None, help="workload width (default 4096)")
     ap.add_argument("--ny", type=int, default=None, help="workload height (default 2048)")
     args = ap.parse_args()
@@ -516,6 +566,8 @@ def main():
         _SIZE["ny"] = args.ny
     if args.warmup < 3:
         args.warmup = 3
+    if args.oracle_procs <= 0:
+        args.oracle_procs = len(os.sched_getaffinity(0))
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -440,12 +440,14 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
     cs.next(P);
     return cs.has;
   };
-  while (body(fA, fB) && body(fB, fA)) {
+  if (cs.has) {  // (every range holds a unit: the grid has at most `total` CTAs)
+    while (body(fA, fB) && body(fB, fA)) {
+    }
   }
 
   if (s_abort && producer) {
     // drain the loads still in flight (bounded) before the CTA exits
-    for (int k = consumed - 1; k < issued; ++k) mbar_wait(smem_u32(&bars[k % S]), (unsigned)((k / S) & 1));
+    for (int k = max(consumed - 1, 0); k < issued; ++k) mbar_wait(smem_u32(&bars[k % S]), (unsigned)((k / S) & 1));
   }
   if (bad) atomicOr(P.flag, 1);
 }

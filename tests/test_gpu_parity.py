@@ -311,6 +311,28 @@ def test_contexts_with_different_fused_rings_coexist(monkeypatch):
     b.close()
 
 
+@pytest.mark.parametrize("nx,ny", [(260, 37), (400, 200), (2048, 300)])
+def test_fused_partition_does_not_change_the_result(monkeypatch, nx, ny):
+    """Which CTA sweeps which rows changes nothing, bit for bit: 1, 2 and the
+    default number of CTAs per SM cut the rows into different ranges (at
+    400 x 200 the default gives every CTA one row)."""
+    w = I.throughput(nx=nx, ny=ny)
+    out = []
+    for ctas in ("1", "2", None):
+        if ctas is None:
+            monkeypatch.delenv("LBM_FUSED_CTAS_PER_SM", raising=False)
+        else:
+            monkeypatch.setenv("LBM_FUSED_CTAS_PER_SM", ctas)
+        p = droplet_pair(w, precision=32, kernel=FUSED, check_every=1)
+        p.gpu.step(6)
+        assert p.gpu.status() == 0
+        out.append((p.gpu.info.tile_blocks, p.gpu.f()))
+        p.close()
+    if nx >= 400:  # 260 x 37 has 70 rows: one per CTA at every setting
+        assert len({b for b, _ in out}) == 3
+    assert all(np.array_equal(out[0][1], f) for _, f in out[1:])
+
+
 @pytest.mark.parametrize("kernel", [FUSED, REF])
 def test_graph_replay_equals_direct_launches(kernel):
     """lbm_step with graphs of 16 steps (on a non-default stream) gives the
