@@ -14,7 +14,8 @@ deg), 5000 steps -- in FP32 with the fused kernel.
   initial density field from pinned memory, K steps, download of the final
   density field, all inside the timed region.
 * roofline: the fused step kernel against the measured HBM copy bandwidth;
-  algorithmic bytes = 72 B per fluid node (9 float loads + 9 float stores).
+  algorithmic bytes = 72 B per fluid node and step (9 float loads + 9 float
+  stores) times the steps one launch performs.
 * cpu_baseline / --impl reference: the FP64 CPU oracle (single thread) on a
   bounded sample of the same workload; --oracle-procs P runs P concurrent
   single-threaded replicas of that sample (0: one per host core) and reports
@@ -363,15 +364,18 @@ def run_ours(args):
             with open(PROFILE_TRAFFIC) as fh:
                 tr = json.load(fh)
             if tr.get("nx") == w.nx and tr.get("ny") == w.ny and tr.get("kernel_sha") == _kernel_sha():
-                traffic = tr["dram_bytes_per_launch"]
+                traffic = tr["dram_bytes_per_step"] * args.steps / max(1, launches)
         except Exception:
             traffic = None
         roof = None
         if kernel_ms:
-            achieved = BYTES_PER_NODE * fluid / (kernel_ms * 1e-3) / 1e9
+            # one launch performs steps / launches steps (CTAs wait on their
+            # neighbours between them)
+            per_launch = BYTES_PER_NODE * fluid * args.steps / max(1, launches)
+            achieved = per_launch / (kernel_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": traffic, "peak_source": peak_kind, "kernel": "k_fused (fused FP32 step)",
-                    "algorithmic_bytes_per_launch": BYTES_PER_NODE * fluid}
+                    "traffic": traffic, "peak_source": peak_kind, "kernel": "k_fused (fused FP32 steps)",
+                    "algorithmic_bytes_per_launch": per_launch, "steps_per_launch": args.steps / max(1, launches)}
         cpu = None
         if ws == 1 and not args.no_cpu:
             v, sample, *_ = cpu_oracle_rate(w, budget_nodes_steps=2.5e7)
