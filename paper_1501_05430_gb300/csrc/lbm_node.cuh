@@ -66,102 +66,6 @@ __device__ __forceinline__ float4 ghost_node(const PT &P, const float *r1, const
   return ghost_value(P, r1[c + 1], r1[c + 2], r1[c + 3], r2[c + 2], gx, top);
 }
 
-// Force (Eq. 9, + Eq. 14), Eq. 17 tensor, MRT collision with the Eq. 6
-// forcing and the Eq. 16 source for one node.  nb[0..8]: (psi, psi^2) at
-// x+e_0..x+e_8; rho: its density; f[9]: its populations; returns f*.  UNIT: every
-// non-conserved rate equals 1 (the relaxation matrix diag(0,1,...,1) of
-// Sec. 3.1), so m* = m_eq + S/2 + C needs only rho and j from f.
-template <bool UNIT, class PT>
-__device__ __forceinline__ void collide_node(const PT &P, const float *f, const float2 *nb, float rho, int y,
-                                             float *fs) {
-  const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
-  const float p0 = nb[0].x;
-  // Eq. 9 (G = -1, U = -psi^2/2) and Eq. 17 (with its G/2 prefactor) weigh
-  // the neighbours' psi and psi^2 with the same two coefficients, so both act
-  // on one combined value per neighbour:
-  //   g_a = (1 - A) psi_0 psi_a + (A/2) psi_a^2
-  //   F   = sum_a w_a g_a e_a,    Q = (-kappa/2) sum_a w_a (g_a - g_0) e_a e_a
-  const float c1 = P.omA * p0;
-  float g[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) g[k] = fmaf(c1, nb[k].x, P.halfA * nb[k].y);
-  const float gd57 = g[5] - g[7], gd86 = g[8] - g[6];
-  float Fx = fmaf(w1, g[1] - g[3], w2 * (gd57 + gd86));
-  float Fy = fmaf(w1, g[2] - g[4], w2 * (gd57 - gd86));
-  if (P.wetting == LBM_WET_MARTYS_CHEN && P.walls) {
-    // Eq. 14 for flat solid rows: sum_a w_a S e_a = (0, -1/2) below, (0, 1/2) above
-    float ssy = (y == 1 ? -0.5f : 0.0f) + (y == P.ny - 2 ? 0.5f : 0.0f);
-    Fy = fmaf(-P.Gw * p0, ssy, Fy);
-  }
-  const float gs57 = g[5] + g[7], gs68 = g[6] + g[8];
-  const float gq = w2 * fmaf(-4.0f, g[0], gs57 + gs68);
-  const float Qxx = P.pre * fmaf(w1, fmaf(-2.0f, g[0], g[1] + g[3]), gq);
-  const float Qyy = P.pre * fmaf(w1, fmaf(-2.0f, g[0], g[2] + g[4]), gq);
-  const float Qxy = P.pre * (w2 * (gs57 - gs68));
-  // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy)
-  const float s13 = f[1] - f[3], s24 = f[2] - f[4];
-  const float d57 = f[5] - f[7], d86 = f[8] - f[6];
-  const float jx = s13 + (d57 + d86);
-  const float jy = s24 + (d57 - d86);
-  // velocity with the half-force shift
-  const float ir = __fdividef(1.0f, rho);
-  const float vx = fmaf(0.5f, Fx, jx) * ir, vy = fmaf(0.5f, Fy, jy) * ir;
-  const float rvx = rho * vx, rvy = rho * vy;
-  const float v2 = fmaf(vx, vx, vy * vy);
-  const float vF = fmaf(vx, Fx, vy * Fy);
-  const float sQ = Qxx + Qyy, dQ = Qxx - Qyy;
-  float es, epss, qxs, qys, pxxs, pxys;
-  if (UNIT) {
-    // m* = m_eq + S/2 + C with s = 1
-    es = fmaf(rho, fmaf(3.0f, v2, -2.0f), fmaf(3.0f, vF, 1.5f * sQ));
-    epss = fmaf(rho, fmaf(-3.0f, v2, 1.0f), -3.0f * vF);
-    qxs = fmaf(-0.5f, Fx, -rvx);
-    qys = fmaf(-0.5f, Fy, -rvy);
-    pxxs = fmaf(rvx, vx, fmaf(-rvy, vy, fmaf(vx, Fx, fmaf(-vy, Fy, -dQ))));
-    pxys = fmaf(rvx, vy, fmaf(0.5f, fmaf(vx, Fy, vy * Fx), -Qxy));
-  } else {
-    const float a13 = f[1] + f[3], a24 = f[2] + f[4];
-    const float ax = a13 + a24, dg = (f[5] + f[6]) + (f[7] + f[8]);
-    const float me = fmaf(-4.0f, f[0], fmaf(2.0f, dg, -ax));
-    const float meps = fmaf(4.0f, f[0], fmaf(-2.0f, ax, dg));
-    const float mqx = fmaf(-2.0f, s13, d57 + d86);
-    const float mqy = fmaf(-2.0f, s24, d57 - d86);
-    const float mpxx = a13 - a24;
-    const float mpxy = (f[5] + f[7]) - (f[6] + f[8]);
-    // relaxation (Eq. 15) with forcing S (Eq. 6) and source C (Eq. 16)
-    es = fmaf(-P.se, fmaf(-rho, fmaf(3.0f, v2, -2.0f), me), me) + fmaf(P.he * 6.0f, vF, 1.5f * P.se * sQ);
-    epss = fmaf(-P.seps, fmaf(-rho, fmaf(-3.0f, v2, 1.0f), meps), meps) - P.heps * 6.0f * vF;
-    qxs = fmaf(-P.sq, mqx + rvx, mqx) - P.hq * Fx;
-    qys = fmaf(-P.sq, mqy + rvy, mqy) - P.hq * Fy;
-    pxxs = fmaf(-P.snu, fmaf(-rvx, vx, fmaf(rvy, vy, mpxx)), mpxx) +
-           fmaf(P.hnu * 2.0f, fmaf(vx, Fx, -vy * Fy), -P.snu * dQ);
-    pxys = fmaf(-P.snu, fmaf(-rvx, vy, mpxy), mpxy) + fmaf(P.hnu, fmaf(vx, Fy, vy * Fx), -P.snu * Qxy);
-  }
-  const float jxs = jx + Fx, jys = jy + Fy;
-  // back to populations: f* = M^T diag(1/N) m*.  rho/9 is rounded through one
-  // correction step: a plain product with a rounded 1/9 biases the mass.
-  const float c9 = 1.0f / 9.0f;
-  float r0 = rho * c9;
-  r0 = fmaf(fmaf(-9.0f, r0, rho), c9, r0);
-  float r1 = es * (1.0f / 36.0f), r2 = epss * (1.0f / 36.0f);
-  float r3 = jxs * (1.0f / 6.0f), r4 = qxs * (1.0f / 12.0f), r5 = jys * (1.0f / 6.0f), r6 = qys * (1.0f / 12.0f);
-  float r7 = pxxs * 0.25f, r8 = pxys * 0.25f;
-  fs[0] = fmaf(4.0f, r2 - r1, r0);
-  float Aax = fmaf(-2.0f, r2, r0 - r1);
-  float Bdg = fmaf(2.0f, r1, r0 + r2);
-  float X1 = fmaf(-2.0f, r4, r3), Y1 = fmaf(-2.0f, r6, r5);
-  fs[1] = (Aax + X1) + r7;
-  fs[3] = (Aax - X1) + r7;
-  fs[2] = (Aax + Y1) - r7;
-  fs[4] = (Aax - Y1) - r7;
-  float X2 = r3 + r4, Y2 = r5 + r6;
-  fs[5] = (Bdg + X2) + (Y2 + r8);
-  fs[6] = (Bdg - X2) + (Y2 - r8);
-  fs[7] = (Bdg - X2) - (Y2 - r8);
-  fs[8] = (Bdg + X2) - (Y2 + r8);
-}
-
-
 // ---- two nodes at once ------------------------------------------------------
 // The same node arithmetic on lane pairs (two nodes of one row that a thread
 // owns) with the packed FP32 instructions of sm_100+: one instruction issues
@@ -174,13 +78,22 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// f[9], psi[9], psi2[9]: lane pairs of the populations and of the neighbour
-// values (psi, psi^2) at x+e_0..x+e_8; rho: the two densities; fs: f*.
+// Force (Eq. 9, + Eq. 14), Eq. 17 tensor, MRT collision with the Eq. 6
+// forcing and the Eq. 16 source for two nodes.  f[9], psi[9], psi2[9]: lane
+// pairs of the populations and of the neighbour values (psi, psi^2) at
+// x+e_0..x+e_8; rho: the two densities; fs: f*.  UNIT: every non-conserved
+// rate equals 1 (the relaxation matrix diag(0,1,...,1) of Sec. 3.1), so
+// m* = m_eq + S/2 + C needs only rho and j from f.
 template <bool UNIT, class PT>
 __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, const float2 *psi, const float2 *psi2,
                                               float2 rho, int y, float2 *fs) {
   const float2 w1 = bc2(1.0f / 3.0f), w2 = bc2(1.0f / 12.0f);
   const float2 p0 = psi[0];
+  // Eq. 9 (G = -1, U = -psi^2/2) and Eq. 17 (with its G/2 prefactor) weigh
+  // the neighbours' psi and psi^2 with the same two coefficients, so both act
+  // on one combined value per neighbour:
+  //   g_a = (1 - A) psi_0 psi_a + (A/2) psi_a^2
+  //   F   = sum_a w_a g_a e_a,    Q = (-kappa/2) sum_a w_a (g_a - g_0) e_a e_a
   const float2 c1 = mul2(bc2(P.omA), p0), hA = bc2(P.halfA);
   float2 g[9];
 #pragma unroll
@@ -189,6 +102,7 @@ __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, cons
   float2 Fx = fma2(w1, sub2(g[1], g[3]), mul2(w2, add2(gd57, gd86)));
   float2 Fy = fma2(w1, sub2(g[2], g[4]), mul2(w2, sub2(gd57, gd86)));
   if (P.wetting == LBM_WET_MARTYS_CHEN && P.walls) {
+    // Eq. 14 for flat solid rows: sum_a w_a S e_a = (0, -1/2) below, (0, 1/2) above
     const float ssy = (y == 1 ? -0.5f : 0.0f) + (y == P.ny - 2 ? 0.5f : 0.0f);
     Fy = fma2(mul2(bc2(-P.Gw), p0), bc2(ssy), Fy);
   }
@@ -198,6 +112,8 @@ __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, cons
   const float2 Qxx = mul2(pre, fma2(w1, fma2(m2, g[0], add2(g[1], g[3])), gq));
   const float2 Qyy = mul2(pre, fma2(w1, fma2(m2, g[0], add2(g[2], g[4])), gq));
   const float2 Qxy = mul2(pre, mul2(w2, sub2(gs57, gs68)));
+  // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy); velocity with the
+  // half-force shift
   const float2 s13 = sub2(f[1], f[3]), s24 = sub2(f[2], f[4]);
   const float2 d57 = sub2(f[5], f[7]), d86 = sub2(f[8], f[6]);
   const float2 jx = add2(s13, add2(d57, d86));
@@ -212,6 +128,7 @@ __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, cons
   const float2 one = bc2(1.0f), three = bc2(3.0f), mthree = bc2(-3.0f), mone = bc2(-1.0f);
   float2 es, epss, qxs, qys, pxxs, pxys;
   if (UNIT) {
+    // m* = m_eq + S/2 + C with s = 1
     es = fma2(rho, fma2(three, v2, bc2(-2.0f)), fma2(three, vF, mul2(bc2(1.5f), sQ)));
     epss = fma2(rho, fma2(mthree, v2, one), mul2(mthree, vF));
     qxs = mul2(mone, fma2(half, Fx, rvx));
@@ -230,6 +147,7 @@ __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, cons
     const float2 mpxx = sub2(a13, a24);
     const float2 mpxy = sub2(add2(f[5], f[7]), add2(f[6], f[8]));
     const float2 se = bc2(P.se), seps = bc2(P.seps), sq = bc2(P.sq), snu = bc2(P.snu);
+    // relaxation (Eq. 15) with forcing S (Eq. 6) and source C (Eq. 16):
     // m* = m - s (m - m_eq) + (1 - s/2) S + C
     const float2 eeq = mul2(rho, fma2(three, v2, bc2(-2.0f)));
     const float2 epseq = mul2(rho, fma2(mthree, v2, one));
@@ -244,6 +162,8 @@ __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, cons
                 fma2(bc2(P.hnu), fma2(vx, Fy, mul2(vy, Fx)), mul2(mul2(mone, snu), Qxy)));
   }
   const float2 jxs = add2(jx, Fx), jys = add2(jy, Fy);
+  // back to populations: f* = M^T diag(1/N) m*.  rho/9 is rounded through one
+  // correction step: a plain product with a rounded 1/9 biases the mass.
   const float2 c9 = bc2(1.0f / 9.0f);
   float2 r0 = mul2(rho, c9);
   r0 = fma2(fma2(bc2(-9.0f), r0, rho), c9, r0);
