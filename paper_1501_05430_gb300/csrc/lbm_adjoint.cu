@@ -385,8 +385,15 @@ __global__ void k_to_double(const R *__restrict__ in, double *__restrict__ out, 
 
 size_t rsize(const lbm_ctx *C) { return C->precision == 64 ? sizeof(double) : sizeof(float); }
 
-// One forward step src -> dst with the reference kernels.
-int ref_step(lbm_ctx *C, const void *src, void *dst) {
+// One forward step src -> dst with the context's own step kernel: the fused
+// FP32 kernel where the context runs it (so the recorded forward advances
+// exactly like lbm_step), else the canonical reference kernels.  The reverse
+// kernels transpose the canonical step at the states this produces.
+int fwd_step(lbm_ctx *C, const void *src, void *dst) {
+  if (C->kernel_in_use == LBM_KERNEL_FUSED) {
+    ACK(lbm_fused_step_between(C, src, dst, &C->launches));
+    return LBM_OK;
+  }
   ACK(lbm_ref_fields(C, src, C->d_fields, &C->launches));
   ACK(lbm_ref_ghost(C, C->d_fields, &C->launches));
   ACK(lbm_ref_collide(C, src, dst, C->d_fields, &C->launches));
@@ -449,7 +456,7 @@ int segment_reverse(lbm_ctx *C, lbm_tape *T, int len, int *lin) {
   char *seg = (char *)T->seg;
   int st = LBM_OK;
   for (int k = 0; k + 1 < len && st == LBM_OK; ++k)
-    st = ref_step(C, seg + (size_t)k * T->state_bytes, seg + (size_t)(k + 1) * T->state_bytes);
+    st = fwd_step(C, seg + (size_t)k * T->state_bytes, seg + (size_t)(k + 1) * T->state_bytes);
   for (int k = len - 1; k >= 0 && st == LBM_OK; --k) {
     st = reverse_step<R>(C, T, seg + (size_t)k * T->state_bytes, *lin);
     *lin ^= 1;
@@ -600,7 +607,7 @@ int lbm_adjoint_record(lbm_ctx *C, int nsteps, int checkpoint_every) {
     lbm_adjoint_free_tape(C);
     return LBM_ENOMEM;
   }
-  // run the steps with the reference kernels, keeping the state at each segment start
+  // run the steps, keeping the state at each segment start
   for (int sg = 0; sg < T->nseg; ++sg) {
     const int len = sg == T->nseg - 1 ? nsteps - sg * T->every : T->every;
     int st = LBM_OK;
@@ -611,7 +618,7 @@ int lbm_adjoint_record(lbm_ctx *C, int nsteps, int checkpoint_every) {
     }
     auto steps = [&](int count, int cur) {
       int r = LBM_OK;
-      for (int k = 0; k < count && r == LBM_OK; ++k) r = ref_step(C, C->f[cur ^ (k & 1)], C->f[cur ^ (k & 1) ^ 1]);
+      for (int k = 0; k < count && r == LBM_OK; ++k) r = fwd_step(C, C->f[cur ^ (k & 1)], C->f[cur ^ (k & 1) ^ 1]);
       return r;
     };
     if (st == LBM_OK && C->stream && len == T->every) {

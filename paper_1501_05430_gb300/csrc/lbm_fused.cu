@@ -552,7 +552,10 @@ int lbm_fused_plan(lbm_ctx *C) {
   return 1;
 }
 
-cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches) {
+namespace {
+
+// Launch arguments of a context's step (all but the destination array).
+FusedArgs fused_args(const lbm_ctx *C) {
   FusedArgs P;
   const lbm_dev_params &D = C->dp;
   const int W = C->tile_w;
@@ -591,13 +594,35 @@ cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches) {
   P.hnu = (float)(1.0 - 0.5 * D.s[7]);
   P.Gw = (float)D.Gw;
   P.coef = C->d_coef;
-  P.fout = (float *)C->f[src ^ 1];
+  P.fout = nullptr;
   P.flag = C->d_flag;
-  const CUtensorMap *tm = (const CUtensorMap *)C->tmaps[2 * src];
-  const CUtensorMap *th = (const CUtensorMap *)C->tmaps[2 * src + 1];
+  return P;
+}
+
+cudaError_t launch_fused(lbm_ctx *C, const CUtensorMap &tm, const CUtensorMap &th, const FusedArgs &P,
+                         unsigned long long *launches) {
   const dim3 grid(C->tile_blocks), block(NCONS);
-  if (C->fused_unit) k_fused<true, kNC><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
-  else k_fused<false, kNC><<<grid, block, C->fused_smem, C->stream>>>(*tm, *th, P);
+  if (C->fused_unit) k_fused<true, kNC><<<grid, block, C->fused_smem, C->stream>>>(tm, th, P);
+  else k_fused<false, kNC><<<grid, block, C->fused_smem, C->stream>>>(tm, th, P);
   ++*launches;
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches) {
+  FusedArgs P = fused_args(C);
+  P.fout = (float *)C->f[src ^ 1];
+  return launch_fused(C, *(const CUtensorMap *)C->tmaps[2 * src], *(const CUtensorMap *)C->tmaps[2 * src + 1], P,
+                      launches);
+}
+
+cudaError_t lbm_fused_step_between(lbm_ctx *C, const void *src, void *dst, unsigned long long *launches) {
+  CUtensorMap tm, th;
+  if (!encode(&tm, const_cast<void *>(src), C->nx, C->ny, C->tile_w) ||
+      !encode(&th, const_cast<void *>(src), C->nx, C->ny, HB))
+    return cudaErrorInvalidValue;
+  FusedArgs P = fused_args(C);
+  P.fout = (float *)dst;
+  return launch_fused(C, tm, th, P, launches);
 }

@@ -81,6 +81,9 @@ cudaError_t lbm_ref_droplets(const lbm_ctx *C, int n, const double *drop, double
 // ---- lbm_fused.cu: single-pass FP32 step ------------------------------------
 int lbm_fused_plan(lbm_ctx *C);  // sets fused_ok, tile_*, tensor maps
 cudaError_t lbm_fused_step(lbm_ctx *C, int src, unsigned long long *launches);
+// The same step between any two state arrays of the context's shape (16-byte
+// aligned): the adjoint's recorded forward and its segment replays.
+cudaError_t lbm_fused_step_between(lbm_ctx *C, const void *src, void *dst, unsigned long long *launches);
 
 // ---- lbm_adjoint.cu: discrete adjoint ---------------------------------------
 void lbm_adjoint_free_tape(lbm_ctx *C);

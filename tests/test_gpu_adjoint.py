@@ -74,11 +74,13 @@ def _reference_gradients(c, wts, steps):
     return np.stack([g(tb).numpy(), g(tt).numpy()]), g(T).item(), f0.grad.numpy()
 
 
-def _lib_gradients(c, wts, steps, every, precision=64):
+def _lib_gradients(c, wts, steps, every, precision=64, kernel=None):
     p = L.lbm_params()
     for name, _ in p._fields_:
         setattr(p, name, getattr(c.params, name))
     p.precision = precision
+    if kernel is not None:
+        p.kernel = kernel
     with L.Lbm(c.nx, c.ny, c.geos, c.T, c.tau, theta=c.theta, walls=c.walls, params=p, torch_state=False) as s:
         s.set_f(c.f0)
         L.lbm_adjoint_record(s.ctx, steps, every)
@@ -117,11 +119,14 @@ def test_checkpoint_interval_does_not_change_the_gradient():
     c.orc.close()
 
 
-def test_fp32_adjoint_close_to_fp64():
+@pytest.mark.parametrize("kernel", [L.LBM_KERNEL_REFERENCE, L.LBM_KERNEL_FUSED])
+def test_fp32_adjoint_close_to_fp64(kernel):
+    """FP32 gradients within 1e-3 of FP64, with the forward recorded and
+    replayed by the canonical FP32 kernels or by the fused kernel."""
     c = _case(32, 14, seed=5)
     wts = np.random.default_rng(6).uniform(-1, 1, (c.ny, c.nx))
     d64 = _lib_gradients(c, wts, 40, 10, 64)
-    d32 = _lib_gradients(c, wts, 40, 10, 32)
+    d32 = _lib_gradients(c, wts, 40, 10, 32, kernel=kernel)
     assert _close(d32[0], d64[0], 1e-3)
     assert d32[1] == pytest.approx(d64[1], rel=1e-3)
     c.orc.close()
@@ -141,10 +146,19 @@ def test_autograd_function_matches_direct_backward():
     c.orc.close()
 
 
-def test_record_advances_like_lbm_step():
+@pytest.mark.parametrize("precision", [64, 32])
+def test_record_advances_like_lbm_step(precision):
+    """The recorded forward runs the context's own step kernel: the canonical
+    kernels in FP64, the fused kernel in FP32 -- the same bits as lbm_step."""
     c = _case(16, 10, seed=2)
-    with L.Lbm(c.nx, c.ny, c.geos, c.T, c.tau, theta=c.theta, params=c.params, torch_state=False) as a, \
-            L.Lbm(c.nx, c.ny, c.geos, c.T, c.tau, theta=c.theta, params=c.params, torch_state=False) as b:
+    p = L.lbm_params()
+    for name, _ in p._fields_:
+        setattr(p, name, getattr(c.params, name))
+    p.precision = precision
+    p.kernel = L.LBM_KERNEL_AUTO
+    with L.Lbm(c.nx, c.ny, c.geos, c.T, c.tau, theta=c.theta, params=p, torch_state=False) as a, \
+            L.Lbm(c.nx, c.ny, c.geos, c.T, c.tau, theta=c.theta, params=p, torch_state=False) as b:
+        assert a.info.kernel_in_use == (L.LBM_KERNEL_FUSED if precision == 32 else L.LBM_KERNEL_REFERENCE)
         a.set_f(c.f0)
         b.set_f(c.f0)
         L.lbm_adjoint_record(a.ctx, 11, 3)
@@ -177,8 +191,9 @@ def _golden():
 
 
 @pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden finite differences not generated")
-@pytest.mark.parametrize("precision,tol", [(64, 1e-3), (32, 1e-2)])
-def test_inversion_gradient_matches_oracle_finite_differences(precision, tol):
+@pytest.mark.parametrize("precision,tol,kernel", [(64, 1e-3, L.LBM_KERNEL_REFERENCE), (32, 1e-2, L.LBM_KERNEL_REFERENCE),
+                                                  (32, 1e-2, L.LBM_KERNEL_FUSED)])
+def test_inversion_gradient_matches_oracle_finite_differences(precision, tol, kernel):
     meta, h_t, rows = _golden()
     ac = I.adjoint_case()
     nx, ny = ac["nx"], ac["ny"]
@@ -187,7 +202,7 @@ def test_inversion_gradient_matches_oracle_finite_differences(precision, tol):
     rv, rl = meta["rho_v"], meta["rho_l"]
     theta = np.full((ny, nx), np.pi / 2)
     theta[0] = ac["theta"]
-    p = L.lbm_params_default(precision=precision, kernel=L.LBM_KERNEL_REFERENCE, check_every=0)
+    p = L.lbm_params_default(precision=precision, kernel=kernel, check_every=0)
     with L.Lbm(nx, ny, eos, T, ac["tau"], theta=theta, params=p, torch_state=False) as s:
         s.set_rho(I.droplet_field(nx, ny, [ac["droplet"]], rv, rl, ac["width"]))
         L.lbm_adjoint_record(s.ctx, ac["steps"], ac["checkpoint_every"])
@@ -202,16 +217,23 @@ def test_inversion_gradient_matches_oracle_finite_differences(precision, tol):
         assert abs(ad - fd) <= tol * max(abs(fd), 1e-3 * ref), (name, idx, ad, fd)
 
 
-def test_graph_replayed_adjoint_equals_direct_launches():
+@pytest.mark.parametrize("precision", [64, 32])
+def test_graph_replayed_adjoint_equals_direct_launches(precision):
     """On a non-default stream the recorded forward and the reverse sweep of
-    every full segment replay captured graphs; same gradients, bit for bit."""
+    every full segment replay captured graphs; same gradients, bit for bit
+    (FP32: forward and replays by the fused kernel)."""
     import torch
 
     c = _case(20, 11, seed=12)
     wts = np.random.default_rng(13).uniform(-1, 1, (c.ny, c.nx))
+    p = L.lbm_params()
+    for name, _ in p._fields_:
+        setattr(p, name, getattr(c.params, name))
+    p.precision = precision
+    p.kernel = L.LBM_KERNEL_AUTO
     out = []
     for stream in (None, torch.cuda.Stream()):
-        with L.Lbm(c.nx, c.ny, c.geos, c.T, c.tau, theta=c.theta, params=c.params, stream=stream,
+        with L.Lbm(c.nx, c.ny, c.geos, c.T, c.tau, theta=c.theta, params=p, stream=stream,
                    torch_state=False) as s:
             s.set_f(c.f0)
             L.lbm_adjoint_record(s.ctx, 27, 8)  # segments 8, 8, 8, 3
