@@ -336,8 +336,8 @@ typedef struct {
 
 /* Launch shape.  Zero fields take the defaults in brackets. */
 typedef struct {
-  int threads;           /* threads per CTA: 256 (the one shape) [256]; thread t owns
-                            columns t and t + 256 of a row */
+  int threads;           /* threads per CTA: 256 (the one shape) [256]; thread t < nx/2
+                            owns columns t and t + nx/2 of a row */
   int ctas_per_sm;       /* cap on resident CTAs per SM [occupancy maximum] */
   int stages;            /* row stages of the shared-memory copy ring, 3..6 [4] */
   int band_rows[4];      /* fluid rows per work item for nx in (0,128], (128,256],

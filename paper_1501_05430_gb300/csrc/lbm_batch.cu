@@ -21,7 +21,8 @@
 // issues, completing on an mbarrier per stage; after acquiring an instance's
 // barrier that thread orders the previous step's generic stores (of this and
 // other CTAs) before its asynchronous-proxy reads with fence.proxy.async.
-// Thread t owns columns t and t + 256 as one lane pair: rho of both with
+// Thread t < h = nx/2 owns columns t and t + h as one lane pair (every lane
+// busy whatever the width; warps past h skip the row work): rho of both with
 // packed adds, psi and psi^2 written to a window laid out in lane pairs, and
 // the node arithmetic of lbm_node.cuh in its packed two-node form -- the same
 // per-node operations as the single-domain fused kernel, so a batch instance
@@ -46,10 +47,10 @@ using lbm_node::collide_node2;
 using lbm_node::eos_node;
 using lbm_node::ghost_value;
 
-constexpr int kNT = 256;       // threads per CTA: thread t owns columns t and t + kNT (one lane pair)
+constexpr int kNT = 256;       // threads per CTA: thread t < nx/2 owns columns t and t + nx/2 (one lane pair)
 constexpr int kMaxNx = 2 * kNT;  // widest instance
 constexpr int kSlots = 4;        // window rows (ring)
-constexpr int kWP = kNT + 2;     // paired window entries e = -1 .. kNT at index e + 1
+constexpr int kWP = kNT + 2;     // paired window entries e = -1 .. nx/2 at index e + 1
 
 // Per-instance block: the node-function fields (same names as the fused
 // kernel's) and the batch bookkeeping.
@@ -146,7 +147,7 @@ __device__ bool wait_ge(const unsigned *p, unsigned target, const int *abort, un
 // Shared memory of a CTA (dynamic part, 128-byte aligned base).
 struct Smem {
   float *stage;              // [S][9][nxs]: rows loaded by bulk copies
-  float2 *wpsi, *wsq;        // [kSlots][kWP]: psi and psi^2 in lane pairs (entry e = columns e, e + kNT)
+  float2 *wpsi, *wsq;        // [kSlots][kWP]: psi and psi^2 in lane pairs (entry e = columns e, e + nx/2)
   float *wrho;               // [nxs + 2]: boundary-row densities, column c at c + 1 (periodic copies at 0, nx + 1)
   unsigned long long *bars;  // [S]: one mbarrier per stage
 };
@@ -171,8 +172,9 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
   const int R = it.y1 - it.y0 + 2;
   const bool geo = P.wetting == LBM_WET_GEOMETRIC;
   const unsigned row_bytes = (unsigned)nx * 4u;
-  const int c0 = tid, c1 = tid + kNT;
-  const bool act0 = c0 < nx, act1 = c1 < nx;  // act1 implies act0
+  const int h = nx >> 1;  // lane-pair offset (nx is a multiple of 4)
+  const int c0 = tid, c1 = tid + h;
+  const bool act0 = tid < h, act1 = act0;  // c1 < nx exactly when c0 < h
 
   int jn = 0;  // next row to load (meaningful in thread 0 only)
   // a stage stays in use until its row is collided (read in the iteration the
@@ -200,16 +202,16 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
   if (tid == 0) issue();
 
   // (psi, psi^2) of column c into a window row pair: lane 0 of entry c and/or
-  // lane 1 of entry c - kNT; columns nx-1 and 0 also fill the periodic
+  // lane 1 of entry c - h; columns nx-1 and 0 also fill the periodic
   // entries -1 and nx
   auto put1 = [&](float2 *ps, float2 *sq, int c, float p, float q) {
-    if (c <= kNT) {
+    if (c <= h) {
       ps[c + 1].x = p;
       sq[c + 1].x = q;
     }
-    if (c >= kNT - 1) {
-      ps[c - kNT + 1].y = p;
-      sq[c - kNT + 1].y = q;
+    if (c >= h - 1) {
+      ps[c - h + 1].y = p;
+      sq[c - h + 1].y = q;
     }
   };
   auto put = [&](float2 *ps, float2 *sq, int c, float p, float q) {
@@ -242,7 +244,7 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
       const float *st = M.stage + (size_t)s * 9 * nxs;
       const bool brow = v == 1 || v == ny - 2;  // boundary row: the ghost rule reads its neighbours
       if (act0) {
-        const float *q0 = st + c0, *q1 = st + (act1 ? c1 : c0);
+        const float *q0 = st + c0, *q1 = st + c1;
         float2 fin[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) fin[a] = make_float2(q0[a * nxs], q1[a * nxs]);
@@ -355,7 +357,7 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
       pn[8] = pm[i + 1];
       qn[8] = qm[i + 1];
       const float *sp = M.stage + (size_t)slot_prev * 9 * nxs;
-      const float *fa = sp + c0, *fb = sp + (act1 ? c1 : c0);
+      const float *fa = sp + c0, *fb = sp + c1;
       float2 fcol[9];
 #pragma unroll
       for (int a = 0; a < 9; ++a) fcol[a] = make_float2(fa[a * nxs], fb[a * nxs]);
