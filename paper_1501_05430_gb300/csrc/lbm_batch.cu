@@ -51,6 +51,7 @@ constexpr int kNT = 256;       // threads per CTA: thread t < nx/2 owns columns 
 constexpr int kMaxNx = 2 * kNT;  // widest instance
 constexpr int kSlots = 4;        // window rows (ring)
 constexpr int kWP = kNT + 2;     // paired window entries e = -1 .. nx/2 at index e + 1
+constexpr int kMaxRing = 16;     // row slots (and mbarriers) of the copy ring at most
 
 // Per-instance block: the node-function fields (same names as the fused
 // kernel's) and the batch bookkeeping.
@@ -146,15 +147,21 @@ __device__ bool wait_ge(const unsigned *p, unsigned target, const int *abort, un
 
 // Shared memory of a CTA (dynamic part, 128-byte aligned base).
 struct Smem {
-  float *stage;              // [S][9][nxs]: rows loaded by bulk copies
+  float *stage;              // S x 9 x nxs floats: rows loaded by bulk copies (K slots of 9 x nx per item)
   float2 *wpsi, *wsq;        // [kSlots][kWP]: psi and psi^2 in lane pairs (entry e = columns e, e + nx/2)
   float *wrho;               // [nxs + 2]: boundary-row densities, column c at c + 1 (periodic copies at 0, nx + 1)
-  unsigned long long *bars;  // [S]: one mbarrier per stage
+  unsigned long long *bars;  // [kMaxRing]: one mbarrier per row slot
 };
 
-// Row loads of the CTA: count k goes to ring slot k % S with mbarrier phase (k / S) & 1.
+// Row loads of the CTA.  The ring is empty between items, so each item
+// repacks the stage memory into K = min(kMaxRing, S nxs / nx) row slots
+// (narrow instances keep more rows in flight); load k of the item goes to
+// slot k % K.  Bit s of wph is the phase parity of the next completion of
+// mbarrier s (every thread keeps the same copy).
 struct Ring {
-  unsigned issued, consumed;
+  unsigned issued, consumed;  // loads of the current item
+  unsigned wph;
+  int K;
 };
 
 // One item of one step: stream virtual rows y0-1 .. y1 (halo and solid rows
@@ -172,6 +179,9 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
   const int R = it.y1 - it.y0 + 2;
   const bool geo = P.wetting == LBM_WET_GEOMETRIC;
   const unsigned row_bytes = (unsigned)nx * 4u;
+  const int K = min(kMaxRing, S * nxs / nx);  // row slots of 9 x nx floats (plane stride nx)
+  rg.issued = rg.consumed = 0u;
+  rg.K = K;
   const int h = nx >> 1;  // lane-pair offset (nx is a multiple of 4)
   const int c0 = tid, c1 = tid + h;
   const bool act0 = tid < h, act1 = act0;  // c1 < nx exactly when c0 < h
@@ -180,22 +190,22 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
   // a stage stays in use until its row is collided (read in the iteration the
   // row arrives and in the next one): rows consumed before the previous
   // iteration are released
-  unsigned released = rg.consumed, start_prev = rg.consumed;
+  unsigned released = 0u, start_prev = 0u;
   auto issue = [&]() {
     // after the generic-proxy reads of the slots being refilled
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    while (jn < R && rg.issued - released < (unsigned)S) {
+    while (jn < R && rg.issued - released < (unsigned)K) {
       const int v = it.y0 - 1 + jn;
       ++jn;
       if (v <= 0 || v >= ny - 1) continue;  // solid rows are not loaded
-      const int s = (int)(rg.issued % (unsigned)S);
+      const int s = (int)(rg.issued % (unsigned)K);
       const unsigned bar = smem_u32(&M.bars[s]);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(9u * row_bytes)
                    : "memory");
-      float *st = M.stage + (size_t)s * 9 * nxs;
+      float *st = M.stage + (size_t)s * 9 * nx;
       const float *row = src + (size_t)v * nx;
 #pragma unroll
-      for (int a = 0; a < 9; ++a) bulk_g2s(smem_u32(st + a * nxs), row + a * n, row_bytes, bar);
+      for (int a = 0; a < 9; ++a) bulk_g2s(smem_u32(st + a * nx), row + a * n, row_bytes, bar);
       ++rg.issued;
     }
   };
@@ -236,18 +246,19 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
     float2 *pcur = M.wpsi + (size_t)(j & 3) * kWP, *qcur = M.wsq + (size_t)(j & 3) * kWP;
     const bool solid = v == 0 || v == ny - 1;
     if (!solid) {
-      const int s = (int)(rg.consumed % (unsigned)S);
+      const int s = (int)(rg.consumed % (unsigned)K);
       slot = s;
-      const unsigned ph = (rg.consumed / (unsigned)S) & 1u;
+      const unsigned ph = (rg.wph >> s) & 1u;
       if (!mbar_wait(smem_u32(&M.bars[s]), ph, wait_ns)) ok = false;
+      rg.wph ^= 1u << s;
       ++rg.consumed;
-      const float *st = M.stage + (size_t)s * 9 * nxs;
+      const float *st = M.stage + (size_t)s * 9 * nx;
       const bool brow = v == 1 || v == ny - 2;  // boundary row: the ghost rule reads its neighbours
       if (act0) {
         const float *q0 = st + c0, *q1 = st + c1;
         float2 fin[9];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) fin[a] = make_float2(q0[a * nxs], q1[a * nxs]);
+        for (int a = 0; a < 9; ++a) fin[a] = make_float2(q0[a * nx], q1[a * nx]);
         const float2 r = add2(add2(add2(add2(fin[0], fin[1]), add2(fin[2], fin[3])),
                                    add2(add2(fin[4], fin[5]), add2(fin[6], fin[7]))),
                               fin[8]);
@@ -356,11 +367,11 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
       qn[7] = qm[i - 1];
       pn[8] = pm[i + 1];
       qn[8] = qm[i + 1];
-      const float *sp = M.stage + (size_t)slot_prev * 9 * nxs;
+      const float *sp = M.stage + (size_t)slot_prev * 9 * nx;
       const float *fa = sp + c0, *fb = sp + c1;
       float2 fcol[9];
 #pragma unroll
-      for (int a = 0; a < 9; ++a) fcol[a] = make_float2(fa[a * nxs], fb[a * nxs]);
+      for (int a = 0; a < 9; ++a) fcol[a] = make_float2(fa[a * nx], fb[a * nx]);
       collide_node2<UNIT>(P, fcol, pn, qn, rp, y, fs);
       push((unsigned)c0, fs[0].x, fs[1].x, fs[2].x, fs[3].x, fs[4].x, fs[5].x, fs[6].x, fs[7].x, fs[8].x);
       if (act1) push((unsigned)c1, fs[0].y, fs[1].y, fs[2].y, fs[3].y, fs[4].y, fs[5].y, fs[6].y, fs[7].y, fs[8].y);
@@ -390,13 +401,13 @@ __global__ void __launch_bounds__(kNT, 3) k_batch(BatchArgs A) {
   const unsigned total = (unsigned)A.steps * (unsigned)A.nitems;
   if (tid == 0) {
     s_timeout = 0;
-    for (int s = 0; s < S; ++s)
+    for (int s = 0; s < kMaxRing; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&M.bars[s])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  Ring rg{0u, 0u};
+  Ring rg{0u, 0u, 0u, 1};
 
   for (;;) {
     if (tid == 0) {
@@ -465,16 +476,21 @@ __global__ void __launch_bounds__(kNT, 3) k_batch(BatchArgs A) {
   }
   // no bulk copy may still be writing into this CTA's shared memory when it
   // exits (only possible after a timeout): wait for them, bounded
-  if (tid == 0)
-    for (unsigned k = rg.consumed; k < rg.issued; ++k)
-      mbar_wait(smem_u32(&M.bars[k % (unsigned)S]), (k / (unsigned)S) & 1u, A.wait_ns);
+  if (tid == 0) {
+    unsigned ph = rg.wph;
+    for (unsigned k = rg.consumed; k < rg.issued; ++k) {
+      const int s = (int)(k % (unsigned)rg.K);
+      mbar_wait(smem_u32(&M.bars[s]), (ph >> s) & 1u, A.wait_ns);
+      ph ^= 1u << s;
+    }
+  }
 }
 
 const void *kernel_ptr() { return (const void *)k_batch; }
 
 size_t smem_bytes(int nxs, int stages) {
   return 128 + (size_t)stages * 9 * nxs * sizeof(float) + (size_t)2 * kSlots * kWP * sizeof(float2) +
-         (size_t)((nxs + 2 + 1) & ~1) * sizeof(float) + (size_t)stages * 8;
+         (size_t)((nxs + 2 + 1) & ~1) * sizeof(float) + (size_t)kMaxRing * 8;
 }
 
 int size_class(int nx) { return nx <= 128 ? 0 : nx <= 256 ? 1 : nx <= 384 ? 2 : 3; }
