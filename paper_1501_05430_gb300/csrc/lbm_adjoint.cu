@@ -29,9 +29,11 @@
 // at a = 0, clamped ghost densities pass nothing.  Gathers instead of atomics
 // keep every sum in a fixed order (the result is reproducible bit for bit).
 //
-// Recording: lbm_adjoint_record runs the steps with the reference kernels and
-// keeps the state every `checkpoint_every` steps; lbm_adjoint_backward
-// replays each segment forward into a segment buffer and then walks it back.
+// Recording: lbm_adjoint_record runs the steps with the context's own step
+// kernel and keeps the state every `checkpoint_every` steps;
+// lbm_adjoint_backward replays each segment forward with the same kernel into
+// a segment buffer and then walks it back (the canonical fields of each
+// state, ghost rows included, are recomputed first).
 #include <math.h>
 #include <string.h>
 
@@ -395,7 +397,6 @@ int fwd_step(lbm_ctx *C, const void *src, void *dst) {
     return LBM_OK;
   }
   ACK(lbm_ref_fields(C, src, C->d_fields, &C->launches));
-  ACK(lbm_ref_ghost(C, C->d_fields, &C->launches));
   ACK(lbm_ref_collide(C, src, dst, C->d_fields, &C->launches));
   return LBM_OK;
 }
@@ -408,7 +409,6 @@ int reverse_step(lbm_ctx *C, lbm_tape *T, const void *f, int lin) {
   const lbm_dev_params &P = C->dp;
   const R *fields = (const R *)C->d_fields;
   ACK(lbm_ref_fields(C, f, C->d_fields, &C->launches));
-  ACK(lbm_ref_ghost(C, C->d_fields, &C->launches));
   R *lam_in = (R *)T->lam[lin], *lam_out = (R *)T->lam[lin ^ 1];
   k_adj_collide<R><<<g, B, 0, C->stream>>>(P, (const R *)f, fields, lam_in, lam_out, (R *)T->aux);
   k_adj_psi<R><<<g, B, 0, C->stream>>>(P, fields, (const R *)T->aux, (R *)T->rhob, T->tacc);

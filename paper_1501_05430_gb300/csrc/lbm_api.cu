@@ -219,7 +219,6 @@ int compute_fields(lbm_ctx *C) {
   int st = ensure_fields(C);
   if (st) return st;
   CK(lbm_ref_fields(C, C->f[C->cur], C->d_fields, &C->launches));
-  CK(lbm_ref_ghost(C, C->d_fields, &C->launches));
   return LBM_OK;
 }
 
@@ -237,12 +236,11 @@ cudaError_t launch_step(lbm_ctx *C, int src, unsigned long long *launches) {
   const int dst = src ^ 1;
   if (C->kernel_in_use == LBM_KERNEL_FUSED) return lbm_fused_step(C, src, launches);
   cudaError_t e = lbm_ref_fields(C, C->f[src], C->d_fields, launches);
-  if (e == cudaSuccess) e = lbm_ref_ghost(C, C->d_fields, launches);
   if (e == cudaSuccess) e = lbm_ref_collide(C, C->f[src], C->f[dst], C->d_fields, launches);
   return e;
 }
 
-int launches_per_step(const lbm_ctx *C) { return C->kernel_in_use == LBM_KERNEL_FUSED ? 1 : 3; }
+int launches_per_step(const lbm_ctx *C) { return C->kernel_in_use == LBM_KERNEL_FUSED ? 1 : 2; }
 
 // Steps per captured graph (even), or 0 when graphs are off or impossible
 // (the legacy default stream cannot be captured).

@@ -69,7 +69,6 @@ struct lbm_ctx {
 // All launchers return the cudaError_t of the launch and add the number of
 // kernels launched to *launches.
 cudaError_t lbm_ref_fields(const lbm_ctx *C, const void *f, void *fields, unsigned long long *launches);
-cudaError_t lbm_ref_ghost(const lbm_ctx *C, void *fields, unsigned long long *launches);
 cudaError_t lbm_ref_collide(const lbm_ctx *C, const void *fin, void *fout, const void *fields,
                             unsigned long long *launches);
 cudaError_t lbm_ref_macro(const lbm_ctx *C, const void *f, const void *fields, double *out7,

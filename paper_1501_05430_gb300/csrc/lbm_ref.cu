@@ -4,10 +4,10 @@
 // with -fmad=false, so that the double instantiation is bit-identical to any
 // IEEE FP64 evaluation of the step in the same order.
 //
-// One step = lbm_ref_fields (rho, psi, U; Eqs. 1, 10, 11) -> lbm_ref_ghost
-// (Eqs. 19-21 or the Martys-Chen zero potential) -> lbm_ref_collide (Eq. 9
-// [+ Eq. 14], Eqs. 16-17, collision Eqs. 4-6 and 15, streaming of Eq. 1 with
-// half-way bounce-back).  The fused FP32 kernel (lbm_fused.cu) computes the
+// One step = lbm_ref_fields (rho, psi, U; Eqs. 1, 10, 11 -- and on the solid
+// rows the ghost values of Eqs. 19-21 or the Martys-Chen zero potential) ->
+// lbm_ref_collide (Eq. 9 [+ Eq. 14], Eqs. 16-17, collision Eqs. 4-6 and 15,
+// streaming of Eq. 1 with half-way bounce-back).  The fused FP32 kernel (lbm_fused.cu) computes the
 // same step in one pass; these kernels also serve the macroscopic getters.
 #include <math.h>
 
@@ -18,68 +18,66 @@ namespace {
 
 using namespace lbm_ref;
 
+// rho at node i: f_0 + f_1 + ... + f_8, left to right.
 template <typename R>
-__global__ void k_fields(lbm_dev_params P, const R *__restrict__ f, R *__restrict__ fields, int *flag) {
+__device__ __forceinline__ R node_rho(const R *__restrict__ f, size_t n, size_t i) {
+  R r = (R)0;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) r = r + f[a * n + i];
+  return r;
+}
+
+// rho, psi, U at every node.  A solid-row node carries its wall's ghost
+// values: Eqs. 19-21 (geometric) from the densities of rows 1-2 (ny-2, ny-3),
+// which the thread sums itself in the same order as their own threads do, or
+// the zero potential (Martys-Chen).
+template <typename R>
+__global__ void k_fields(lbm_dev_params P, const R *__restrict__ f, const double *__restrict__ coef,
+                         R *__restrict__ fields, int *flag) {
   Mdl<R> m(P);
   size_t n = (size_t)m.nx * m.ny;
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int y = (int)(i / m.nx);
-  if (m.solid_row(y)) return;
-  R r = (R)0;
-#pragma unroll
-  for (int a = 0; a < 9; ++a) r = r + f[a * n + i];
+  if (m.solid_row(y)) {
+    const int x = (int)(i - (size_t)y * m.nx);
+    R g = (R)0, psi = (R)0, U = (R)0;
+    if (m.wetting != LBM_WET_MARTYS_CHEN) {
+      const int w = y == 0 ? 0 : 1, y1 = w == 0 ? 1 : m.ny - 2, y2 = w == 0 ? 2 : m.ny - 3;
+      const R rim1 = node_rho(f, n, (size_t)y1 * m.nx + m.wx(x - 1));
+      const R rip1 = node_rho(f, n, (size_t)y1 * m.nx + m.wx(x + 1));
+      const R ri1 = node_rho(f, n, (size_t)y1 * m.nx + x);
+      const R ri2 = node_rho(f, n, (size_t)y2 * m.nx + x);
+      const R c = (R)coef[w * m.nx + x];
+      const R cot = (R)coef[2 * m.nx + w * m.nx + x];
+      const R a = rip1 - rim1;
+      if (m.n_iter <= 0) {
+        g = ri2 + cot * fabs(a);
+      } else {
+        R d = (R)2 * (ri2 - ri1);
+        g = ri2;
+        for (int k = 0; k < m.n_iter; ++k) {
+          R s = a * a + d * d;
+          g = ri2 + c * sqrt(s);
+          d = ri2 - g;
+        }
+      }
+      g = fmin(fmax(g, (R)0), m.ghost_max);
+      // at rho_max (the root of U, Eq. 10) psi and U take their exact value 0
+      if (g < m.rho_max) psi_U(m, g, psi, U);
+    }
+    fields[i] = g;
+    fields[n + i] = psi;
+    fields[2 * n + i] = U;
+    return;
+  }
+  const R r = node_rho(f, n, i);
   R psi, U;
   psi_U(m, r, psi, U);
   fields[i] = r;
   fields[n + i] = psi;
   fields[2 * n + i] = U;
   if (!(r > (R)0) || r > m.rho_max) atomicOr(flag, 1);
-}
-
-// Eqs. 19-21 (geometric) or zero potential (Martys-Chen) on the solid rows.
-template <typename R>
-__global__ void k_ghost(lbm_dev_params P, const double *__restrict__ coef, R *__restrict__ fields) {
-  Mdl<R> m(P);
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * m.nx) return;
-  int w = t / m.nx, x = t - w * m.nx;
-  size_t n = (size_t)m.nx * m.ny;
-  int yg = w == 0 ? 0 : m.ny - 1, y1 = w == 0 ? 1 : m.ny - 2, y2 = w == 0 ? 2 : m.ny - 3;
-  size_t ig = (size_t)yg * m.nx + x;
-  if (m.wetting == LBM_WET_MARTYS_CHEN) {
-    fields[ig] = (R)0;
-    fields[n + ig] = (R)0;
-    fields[2 * n + ig] = (R)0;
-    return;
-  }
-  const R *rho = fields;
-  R rim1 = rho[(size_t)y1 * m.nx + m.wx(x - 1)];
-  R rip1 = rho[(size_t)y1 * m.nx + m.wx(x + 1)];
-  R ri1 = rho[(size_t)y1 * m.nx + x];
-  R ri2 = rho[(size_t)y2 * m.nx + x];
-  R c = (R)coef[w * m.nx + x];
-  R cot = (R)coef[2 * m.nx + w * m.nx + x];
-  R a = rip1 - rim1;
-  R g;
-  if (m.n_iter <= 0) {
-    g = ri2 + cot * fabs(a);
-  } else {
-    R d = (R)2 * (ri2 - ri1);
-    g = ri2;
-    for (int k = 0; k < m.n_iter; ++k) {
-      R s = a * a + d * d;
-      g = ri2 + c * sqrt(s);
-      d = ri2 - g;
-    }
-  }
-  g = fmin(fmax(g, (R)0), m.ghost_max);
-  // at rho_max (the root of U, Eq. 10) psi and U take their exact value 0
-  R psi = (R)0, U = (R)0;
-  if (g < m.rho_max) psi_U(m, g, psi, U);
-  fields[ig] = g;
-  fields[n + ig] = psi;
-  fields[2 * n + ig] = U;
 }
 
 template <typename R>
@@ -208,19 +206,11 @@ inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 cudaError_t lbm_ref_fields(const lbm_ctx *C, const void *f, void *fields, unsigned long long *launches) {
   size_t n = (size_t)C->nx * C->ny;
   if (C->precision == 64)
-    k_fields<double><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, (const double *)f, (double *)fields, C->d_flag);
+    k_fields<double><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, (const double *)f, C->d_coef, (double *)fields,
+                                                          C->d_flag);
   else
-    k_fields<float><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, (const float *)f, (float *)fields, C->d_flag);
-  ++*launches;
-  return cudaGetLastError();
-}
-
-cudaError_t lbm_ref_ghost(const lbm_ctx *C, void *fields, unsigned long long *launches) {
-  if (!C->walls) return cudaSuccess;
-  if (C->precision == 64)
-    k_ghost<double><<<nblk(2 * C->nx, 128), 128, 0, C->stream>>>(C->dp, C->d_coef, (double *)fields);
-  else
-    k_ghost<float><<<nblk(2 * C->nx, 128), 128, 0, C->stream>>>(C->dp, C->d_coef, (float *)fields);
+    k_fields<float><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, (const float *)f, C->d_coef, (float *)fields,
+                                                         C->d_flag);
   ++*launches;
   return cudaGetLastError();
 }
