@@ -575,6 +575,7 @@ void lbm_adjoint_free_tape(lbm_ctx *C) {
 extern "C" {
 
 int lbm_adjoint_record(lbm_ctx *C, int nsteps, int checkpoint_every) {
+  LbmRange nvtx_range("lbm_adjoint_record");
   if (!C || nsteps < 1 || checkpoint_every < 1) return LBM_EINVAL;
   if (C->status) return C->status;
   if (C->dp.n_iter > kMaxIter) return LBM_EUNSUPPORTED;
@@ -652,6 +653,7 @@ int lbm_adjoint_record(lbm_ctx *C, int nsteps, int checkpoint_every) {
 }
 
 int lbm_adjoint_backward(lbm_ctx *C, const double *dl_drho, double *dl_dtheta, double *dl_dT, double *dl_df0) {
+  LbmRange nvtx_range("lbm_adjoint_backward");
   if (!C || !dl_drho) return LBM_EINVAL;
   if (!C->tape) return LBM_EINVAL;
   if (C->status == LBM_ECUDA) return C->status;

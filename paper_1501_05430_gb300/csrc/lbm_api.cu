@@ -532,6 +532,7 @@ int lbm_init_droplets(lbm_ctx *C, int n, const double *xc, const double *radius,
 }
 
 int lbm_step(lbm_ctx *C, int nsteps) {
+  LbmRange nvtx_range("lbm_step");
   if (!C || nsteps < 0) return LBM_EINVAL;
   if (C->status) return C->status;
   const int G = graph_steps(C);

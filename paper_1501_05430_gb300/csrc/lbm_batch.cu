@@ -868,6 +868,7 @@ int lbm_batch_set_config(lbm_batch *B, const lbm_batch_config *cfg) {
 }
 
 int lbm_batch_step(lbm_batch *B, int nsteps) {
+  LbmRange nvtx_range("lbm_batch_step");
   if (!B || nsteps < 0) return LBM_EINVAL;
   if (B->status) return B->status;
   if (nsteps == 0) return LBM_OK;
@@ -909,6 +910,7 @@ int lbm_batch_contact_angles(lbm_batch *B, int wall, double *theta, double *H, d
 }
 
 int lbm_batch_autotune(lbm_batch *B, int trial_steps, lbm_batch_config *best) {
+  LbmRange nvtx_range("lbm_batch_autotune");
   if (!B || trial_steps < 2) return LBM_EINVAL;
   if (B->status) return B->status;
   trial_steps += trial_steps & 1;  // every trial ends on the parity it started from

@@ -2,9 +2,19 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/lbm.h"
+
+// NVTX range over a scope (the library's entry points), so that a profiler
+// timeline shows which call launched which kernels; free without a tool.
+struct LbmRange {
+  explicit LbmRange(const char *name) { nvtxRangePushA(name); }
+  ~LbmRange() { nvtxRangePop(); }
+  LbmRange(const LbmRange &) = delete;
+  LbmRange &operator=(const LbmRange &) = delete;
+};
 
 // Device-side model constants, passed by value to every kernel.
 // The EOS and model parameters are kept in double; kernels of the float

@@ -76,3 +76,22 @@ def test_single_process_helpers_need_no_process_group():
 
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert bench.job_mlups(1, 4096 * 2046, 5000, 0.574) == pytest.approx(4096 * 2046 * 5000 / 0.574 / 1e6)
+
+
+def test_reference_arm_times_concurrent_oracle_replicas():
+    """--impl reference --oracle-procs 2: two single-threaded oracle replicas of
+    the sample run at once (spawned processes) and the line reports their
+    aggregate rate with cores = 2."""
+    import json
+    import subprocess
+
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--nx", "64", "--ny", "32",
+           "--steps", "2", "--warmup", "3", "--oracle-procs", "2"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "MLUPS"
+    assert d["cpu_baseline"]["cores"] == 2 and d["cpu_baseline"]["value"] == d["value"]
+    assert "2 concurrent single-threaded replicas" in d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["oracle_status"] == 0
