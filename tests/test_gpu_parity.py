@@ -15,7 +15,7 @@ import oracle as O
 from paper_1501_05430_gb300 import inputs as I
 from paper_1501_05430_gb300 import lbm as L
 
-from helpers import Pair, droplet_pair
+from helpers import Case, Pair, droplet_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -163,6 +163,39 @@ def test_fp32_fused_full_size_throughput_workload():
     fl = np.broadcast_to(_fluid(w.ny)[:, None], rg.shape)
     assert _rel(rg, ro, fl) < 1e-5
     p.close()
+
+
+def test_fp32_fused_at_the_32_bit_offset_limit():
+    """The largest grid the fused kernel takes (9 nx ny just below 2^31, where
+    its 32-bit element offsets end): 32768 x 7281, 17 GB of distributions.
+    The initial state and the wall angles repeat every 256 columns, so after 2
+    steps every 256-column window equals the oracle run on a 256-wide periodic
+    domain (x translation symmetry holds at any size); three windows are
+    compared node by node."""
+    tile, reps, ny = 256, 128, 7281
+    nx = tile * reps
+    assert 9 * nx * ny < 2 ** 31 <= 9 * nx * (ny + 1)
+    w = I.throughput(nx=tile, ny=ny)
+    c = Case(tile, ny, t_over_tc=w.t_over_tc, tau=w.tau, theta=w.theta, rates=w.rates, precision=32,
+             eos=w.eos, A=w.A, kappa=w.kappa, kernel=FUSED)
+    rho_tile = I.droplet_field(tile, ny, w.droplets, c.rho_v, c.rho_l, w.width)
+    c.orc.set_rho(rho_tile)
+    assert c.orc.step(2) == 0
+    ro = c.orc.rho()
+    g = L.Lbm(nx, ny, c.geos, c.T, c.tau, theta=np.tile(c.theta, (1, reps)), params=c.params, torch_state=False)
+    try:
+        assert g.info.kernel_in_use == FUSED
+        g.set_rho(np.tile(rho_tile, (1, reps)))
+        g.step(2)
+        assert g.status() == 0
+        rg = g.rho()
+    finally:
+        g.close()
+        c.orc.close()
+    fl = np.broadcast_to(_fluid(ny)[:, None], ro.shape)
+    for k in (0, reps // 2, reps - 1):
+        win = rg[:, k * tile:(k + 1) * tile]
+        assert _rel(win, ro, fl) < 1e-5, k
 
 
 # ---------------------------------------------------------------------------
