@@ -81,9 +81,12 @@ def _variant_pair(name, nx, ny, precision, kernel, seed=5):
     return p, walls
 
 
+@pytest.mark.parametrize("nx,ny", [(28, 16), (4, 5)])
 @pytest.mark.parametrize("name", list(VARIANTS))
-def test_fp64_variants_bit_exact(name):
-    p, walls = _variant_pair(name, 28, 16, 64, REF)
+def test_fp64_variants_bit_exact(name, nx, ny):
+    """Every model variant, and the smallest grid the library takes (4 x 5:
+    three fluid rows, both ghost rules reading row 2)."""
+    p, walls = _variant_pair(name, nx, ny, 64, REF)
     for _ in range(3):
         assert p.step(2) == 0
         assert np.array_equal(p.gpu.f(), p.orc.get_f())
@@ -123,11 +126,13 @@ def test_fp32_fused_single_droplet_1000_steps():
     p.close()
 
 
-@pytest.mark.parametrize("nx,ny", [(100, 40), (260, 24), (8, 9), (132, 7)])
+@pytest.mark.parametrize("nx,ny", [(100, 40), (260, 24), (8, 9), (132, 7), (4, 5)])
 @pytest.mark.parametrize("name", list(VARIANTS))
 def test_fp32_fused_variants(name, nx, ny):
-    """Ragged strips (nx not a multiple of 128), tiny grids and every model
-    variant: FP32 fused vs FP64 oracle after 12 steps."""
+    """Ragged strips (nx not a multiple of 128), tiny grids down to the
+    smallest the library takes (4 x 5: one 4-column strip whose halo boxes
+    wrap onto itself) and every model variant: FP32 fused vs FP64 oracle after
+    12 steps."""
     p, walls = _variant_pair(name, nx, ny, 32, FUSED, seed=nx + ny)
     assert p.gpu.info.kernel_in_use == FUSED
     assert p.step(12) == 0
@@ -162,6 +167,17 @@ def test_fp32_fused_full_size_throughput_workload():
     rg, ro = p.gpu.rho(), p.orc.rho()
     fl = np.broadcast_to(_fluid(w.ny)[:, None], rg.shape)
     assert _rel(rg, ro, fl) < 1e-5
+    p.close()
+
+
+@pytest.mark.parametrize("kernel", [FUSED, REF])
+def test_zero_steps_change_nothing(kernel):
+    """lbm_step(ctx, 0) launches nothing and leaves the state as it was."""
+    p, _ = _variant_pair("geometric_random_theta", 16, 9, 32, kernel)
+    f0, l0 = p.gpu.f(), p.gpu.launches()
+    p.gpu.step(0)
+    assert p.gpu.launches() == l0 and p.gpu.info.steps_done == 0
+    assert np.array_equal(p.gpu.f(), f0)
     p.close()
 
 
