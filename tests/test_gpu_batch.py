@@ -31,6 +31,8 @@ SPECS = [
     (132, 24, dict(t_over_tc=0.55, tau=0.7, rates=dict(s_e=0.8, s_eps=0.8, s_j=1.0, s_q=1.1), theta="random")),
     (64, 9, dict(theta="random", n_iter=8, tau=0.7)),
     (384, 14, dict(theta="random", t_over_tc=0.7, tau=0.9)),
+    (4, 5, dict(theta="random")),            # the smallest instance: one lane pair per row, 16 ring slots
+    (12, 6, dict(wetting=1, G_w=-0.1)),
 ]
 
 
