@@ -339,7 +339,9 @@ typedef struct {
   int threads;           /* threads per CTA: 256 (the one shape) [256]; thread t < nx/2
                             owns columns t and t + nx/2 of a row */
   int ctas_per_sm;       /* cap on resident CTAs per SM [occupancy maximum] */
-  int stages;            /* row stages of the shared-memory copy ring, 3..6 [4] */
+  int stages;            /* shared memory of the copy ring, in rows of the widest
+                            instance, 3..6 [4]; each work item repacks it into
+                            min(16, stages x widest / nx) rows of its own width */
   int band_rows[4];      /* fluid rows per work item for nx in (0,128], (128,256],
                             (256,384], (384, ...) [32 each] */
   int steps_per_launch;  /* steps advanced by one launch [16] */
