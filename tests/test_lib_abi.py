@@ -89,3 +89,22 @@ def test_fp64_units_compiled_without_fma_contraction():
     """The canonical-order units must be built with -fmad=false."""
     assert "-fmad=false" in B.UNITS["lbm_ref.cu"]
     assert "-fmad=false" in B.UNITS["lbm_measure.cu"]
+
+
+def test_required_state_bytes():
+    """Two copies of the 9 nx ny distributions in the given precision; 0 for
+    sizes or precisions the library does not take."""
+    assert L.lbm_required_state_bytes(4096, 2048, 32) == 2 * 9 * 4096 * 2048 * 4
+    assert L.lbm_required_state_bytes(100, 60, 64) == 2 * 9 * 100 * 60 * 8
+    assert L.lbm_required_state_bytes(0, 60, 32) == 0
+    assert L.lbm_required_state_bytes(100, 60, 16) == 0
+
+
+def test_batch_config_default_leaves_every_choice_to_the_library():
+    """All shape fields 0 (the library's defaults apply) and no held instance."""
+    c = L.lbm_batch_config_default()
+    assert c.threads == 0 and c.ctas_per_sm == 0 and c.stages == 0 and list(c.band_rows) == [0, 0, 0, 0]
+    assert c.steps_per_launch == 0 and c.graph_launches == 0 and c.wait_seconds == 0.0
+    assert c.hold_instance == -1
+    c2 = L.lbm_batch_config_default(stages=5, band_rows=[8, 16, 32, 64])
+    assert c2.stages == 5 and list(c2.band_rows) == [8, 16, 32, 64]
