@@ -223,3 +223,29 @@ def test_instability_is_flagged():
     rho[5, 7] = -0.1
     s.set_rho(rho)
     assert s.step(1) == -4
+
+
+@pytest.mark.parametrize("rates", [None, dict(s_rho=0.0, s_e=0.8, s_eps=0.9, s_j=1.0, s_q=1.1, s_nu=1 / 0.9)])
+def test_uniform_flow_is_a_fixed_point(rates):
+    """A uniform density moving at a uniform velocity through a periodic box is
+    a fixed point of the whole step: uniform psi and U give no force and no
+    Eq. 16 source, the collision leaves the second-order equilibrium
+    w_a rho [1 + 3 e.v + 9/2 (e.v)^2 - 3/2 v^2] unchanged at any rates, and
+    streaming moves a uniform field onto itself -- which pins the
+    velocity-dependent equilibrium moments (signs included)."""
+    T = 0.8 * TC
+    rv, _ = O.coexistence(CS, T)
+    v = np.array([0.05, -0.03])
+    e = np.array(E, float)
+    w = np.array([float(x) for x in WEQ])
+    ev = e @ v
+    feq = w * rv * (1 + 3 * ev + 4.5 * ev ** 2 - 1.5 * (v @ v))
+    nx, ny = 12, 8
+    f0 = np.broadcast_to(feq[:, None, None], (9, ny, nx)).copy()
+    kw = {} if rates is None else dict(rates=rates)
+    s = O.Sim(nx, ny, CS, T, tau=0.9, walls=False, **kw)
+    s.set_f(f0)
+    assert s.step(3) == 0
+    f = s.get_f()
+    s.close()
+    assert np.abs(f - f0).max() < 1e-14 * f0.max()
