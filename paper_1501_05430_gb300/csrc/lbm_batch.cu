@@ -16,11 +16,14 @@
 // batch abort word, and every CTA leaves at its next entry.  Instances never
 // wait on each other.
 //
-// Rows are streamed through a ring of shared-memory stages by one-dimensional
+// Rows are streamed through a ring of shared-memory slots by one-dimensional
 // bulk copies (cp.async.bulk, 9 per row, one per plane) that one thread
-// issues, completing on an mbarrier per stage; after acquiring an instance's
-// barrier that thread orders the previous step's generic stores (of this and
-// other CTAs) before its asynchronous-proxy reads with fence.proxy.async.
+// issues, completing on an mbarrier per slot; the ring's memory (S rows of the
+// widest instance) is repacked for each item into as many rows of that
+// instance's width as fit (at most 16), so narrow instances keep more rows in
+// flight.  After acquiring an instance's barrier that thread orders the
+// previous step's generic stores (of this and other CTAs) before its
+// asynchronous-proxy reads with fence.proxy.async.
 // Thread t < h = nx/2 owns columns t and t + h as one lane pair (every lane
 // busy whatever the width; warps past h skip the row work): rho of both with
 // packed adds, psi and psi^2 written to a window laid out in lane pairs, and
