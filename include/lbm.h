@@ -136,6 +136,21 @@ int lbm_eos_critical(const lbm_eos *eos, double *Tc, double *rho_c);
  * ignored).  LBM_EINVAL when no solution exists. */
 int lbm_coexistence(const lbm_eos *eos, double T, double *rho_v, double *rho_l);
 
+/* The density bounds lbm_create derives for a context whose params.rho_max
+ * and params.rho_mid are 0, computed on the host (no device call):
+ *  rho_v, rho_l: the coexistence densities of lbm_coexistence;
+ *  rho_max:      the smallest rho > rho_l with p(rho) = rho/3, i.e. where
+ *                psi^2 = 2 (rho/3 - p) of Eq. 10 (c = 1, G = -1) returns to 0
+ *                (Brent's method on the Carnahan-Starling branch; the linear
+ *                liquid branch of Eq. 11 in closed form, DBL_MAX when its slope
+ *                theta_l is <= 1/3 and psi^2 stays positive).  It is the upper
+ *                clamp of the Eqs. 19-21 ghost densities and the instability
+ *                bound of lbm_step;
+ *  rho_mid:      (rho_v + rho_l)/2, the contour of lbm_contact_angle.
+ * Any output pointer may be NULL.  LBM_EINVAL as for lbm_coexistence. */
+int lbm_eos_bounds(const lbm_eos *eos, double T, double *rho_v, double *rho_l, double *rho_max,
+                   double *rho_mid);
+
 /* Create a context on the current CUDA device.
  *  nx >= 4, ny >= 5; tau > 1/2 (viscous rate s_nu = 1/tau unless set).
  *  eos, T: equation of state and absolute temperature (for Carnahan-Starling

@@ -163,6 +163,16 @@ double eos_rho_max(const lbm_eos &e, double T, double rl) {
   return root > rl ? root : DBL_MAX;
 }
 
+// Coexistence densities and the derived bounds of a context (lbm_eos_bounds).
+int eos_bounds(const lbm_eos &e, double T, double *rv, double *rl, double *rmax, double *rmid) {
+  int st = e.kind == LBM_EOS_CARNAHAN_STARLING ? cs_coexistence(CS{e.a, e.b, e.R}, T, rv, rl)
+                                               : pw_coexistence(e, rv, rl);
+  if (st != LBM_OK) return LBM_EINVAL;
+  *rmax = eos_rho_max(e, T, *rl);
+  *rmid = 0.5 * (*rv + *rl);
+  return LBM_OK;
+}
+
 int validate_eos(const lbm_eos *e) {
   if (!e) return LBM_EINVAL;
   if (e->kind == LBM_EOS_CARNAHAN_STARLING) {
@@ -300,13 +310,8 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
       walls = 1;
     }
   }
-  double rv = 0, rl = 0;
-  if (eos->kind == LBM_EOS_CARNAHAN_STARLING) {
-    CS cs{eos->a, eos->b, eos->R};
-    if (cs_coexistence(cs, T, &rv, &rl) != LBM_OK) return LBM_EINVAL;
-  } else {
-    if (pw_coexistence(*eos, &rv, &rl) != LBM_OK) return LBM_EINVAL;
-  }
+  double rv = 0, rl = 0, rmax = 0, rmid = 0;
+  if (eos_bounds(*eos, T, &rv, &rl, &rmax, &rmid) != LBM_OK) return LBM_EINVAL;
   if (theta && walls) {
     for (int x = 0; x < nx; ++x) {
       double tb = theta[x], tt = theta[(size_t)(ny - 1) * nx + x];
@@ -327,8 +332,8 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
   C->params = P;
   C->rho_v = rv;
   C->rho_l = rl;
-  C->rho_max = P.rho_max > 0 ? P.rho_max : eos_rho_max(*eos, T, rl);
-  C->rho_mid = P.rho_mid > 0 ? P.rho_mid : 0.5 * (rv + rl);
+  C->rho_max = P.rho_max > 0 ? P.rho_max : rmax;
+  C->rho_mid = P.rho_mid > 0 ? P.rho_mid : rmid;
   C->ghost_max = P.rho_ghost_max > 0 ? fmin(P.rho_ghost_max, C->rho_max) : C->rho_max;
   C->stream = (cudaStream_t)stream;
   lbm_dev_params &D = C->dp;
@@ -473,6 +478,17 @@ int lbm_coexistence(const lbm_eos *eos, double T, double *rho_v, double *rho_l) 
   if (!eos || !rho_v || !rho_l || validate_eos(eos)) return LBM_EINVAL;
   if (eos->kind == LBM_EOS_CARNAHAN_STARLING) return cs_coexistence(CS{eos->a, eos->b, eos->R}, T, rho_v, rho_l);
   return pw_coexistence(*eos, rho_v, rho_l);
+}
+
+int lbm_eos_bounds(const lbm_eos *eos, double T, double *rho_v, double *rho_l, double *rho_max, double *rho_mid) {
+  if (!eos || validate_eos(eos)) return LBM_EINVAL;
+  double v[4];
+  int st = eos_bounds(*eos, T, &v[0], &v[1], &v[2], &v[3]);
+  if (st) return st;
+  double *out[4] = {rho_v, rho_l, rho_max, rho_mid};
+  for (int k = 0; k < 4; ++k)
+    if (out[k]) *out[k] = v[k];
+  return LBM_OK;
 }
 
 size_t lbm_required_state_bytes(int nx, int ny, int precision) {

@@ -90,6 +90,7 @@ _SIGS = {
     "lbm_params_default": (c_int, [ctypes.POINTER(lbm_params)]),
     "lbm_eos_critical": (c_int, [ctypes.POINTER(lbm_eos), DP, DP]),
     "lbm_coexistence": (c_int, [ctypes.POINTER(lbm_eos), c_double, DP, DP]),
+    "lbm_eos_bounds": (c_int, [ctypes.POINTER(lbm_eos), c_double, DP, DP, DP, DP]),
     "lbm_create": (c_int, [c_int, c_int, ctypes.POINTER(lbm_eos), c_double, c_double, DP, c_void_p,
                            ctypes.POINTER(lbm_params), c_void_p, ctypes.POINTER(c_void_p)]),
     "lbm_required_state_bytes": (c_size_t, [c_int, c_int, c_int]),
@@ -211,6 +212,13 @@ def lbm_coexistence(eos: lbm_eos, T: float = 0.0):
     rv, rl = c_double(), c_double()
     _check(load().lbm_coexistence(ctypes.byref(eos), T, ctypes.byref(rv), ctypes.byref(rl)), "lbm_coexistence")
     return rv.value, rl.value
+
+
+def lbm_eos_bounds(eos: lbm_eos, T: float = 0.0):
+    """(rho_v, rho_l, rho_max, rho_mid) that lbm_create derives for this EOS and T."""
+    v = [c_double() for _ in range(4)]
+    _check(load().lbm_eos_bounds(ctypes.byref(eos), T, *[ctypes.byref(x) for x in v]), "lbm_eos_bounds")
+    return tuple(x.value for x in v)
 
 
 def lbm_required_state_bytes(nx, ny, precision) -> int:

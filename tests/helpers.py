@@ -28,11 +28,16 @@ def resolve_rates(tau, rates=None):
 class Case:
     """The inputs of one simulation on both sides: the oracle Sim and the
     liblbm parameters (lbm_params, EOS, T, tau, theta) built from the same
-    numbers."""
+    numbers.
+
+    The library derives its own density bounds (rho_max: ghost clamp and
+    instability bound; rho_mid: the angle contour) from the EOS, as a user's
+    context does; the oracle's values go into lbm_params only with
+    oracle_bounds=True."""
 
     def __init__(self, nx, ny, *, t_over_tc=0.8, tau=1.0, eos="cs", pw=None, theta=np.pi / 2, walls=True,
                  A=-0.6, kappa=0.5, G_w=0.0, n_iter=4, wetting=0, rates=None, precision=64,
-                 kernel=L.LBM_KERNEL_AUTO, check_every=0):
+                 kernel=L.LBM_KERNEL_AUTO, check_every=0, oracle_bounds=False):
         self.nx, self.ny, self.tau, self.walls = nx, ny, tau, walls
         if eos == "pw":
             eos = dict(kind="pw", theta_v=pw[0], theta_m=pw[1], theta_l=pw[2], rho1=pw[3], rho2=pw[4])
@@ -57,8 +62,10 @@ class Case:
                          n_iter=n_iter, wetting=wetting, theta=self.theta, rates=r, rho_max_=self.rho_max)
         self.params = L.lbm_params_default(A=A, kappa=kappa, G_w=G_w, n_iter=n_iter, wetting=wetting,
                                            precision=precision, kernel=kernel, s_e=r["s_e"], s_eps=r["s_eps"],
-                                           s_j=r["s_j"], s_q=r["s_q"], s_nu=r["s_nu"], check_every=check_every,
-                                           rho_max=min(self.rho_max, 1e300), rho_mid=self.rho_mid)
+                                           s_j=r["s_j"], s_q=r["s_q"], s_nu=r["s_nu"], check_every=check_every)
+        if oracle_bounds:
+            self.params.rho_max = min(self.rho_max, 1e300)
+            self.params.rho_mid = self.rho_mid
 
     def desc(self):
         """Instance description for lbm_batch_create (FP32)."""

@@ -76,6 +76,38 @@ def test_piecewise_coexistence_matches_oracle(ratio, tv, tm, tl):
     assert rl == pytest.approx(ratio, rel=1e-9)
 
 
+@pytest.mark.parametrize("a", [1.0, 0.25])
+@pytest.mark.parametrize("tr", [0.5, 0.6, 0.7, 0.8])
+def test_library_density_bounds_match_oracle_cs(a, tr):
+    """The bounds lbm_create derives by itself (no override in lbm_params):
+    rho_max, the smallest root of p(rho) = rho/3 above rho_l (Eq. 10: psi^2 >= 0
+    below it; the ghost-density clamp and the instability bound), and rho_mid,
+    the contour of the angle measurement, equal the oracle's bisection root and
+    coexistence midpoint."""
+    oeos = O.carnahan_starling(a, 4.0, 1.0)
+    T = tr * O.cs_critical(oeos)[0]
+    orv, orl = O.coexistence(oeos, T)
+    rv, rl, rmax, rmid = L.lbm_eos_bounds(L.carnahan_starling(a, 4.0, 1.0), T)
+    assert rmax == pytest.approx(O.rho_max(oeos, T, orl), rel=1e-12)
+    assert rmid == pytest.approx(0.5 * (orv + orl), rel=1e-12)
+    assert rl < rmax < 1.0  # 4/b is the packing limit of Carnahan-Starling
+    assert (rv, rl) == L.lbm_coexistence(L.carnahan_starling(a, 4.0, 1.0), T)
+
+
+@pytest.mark.parametrize("ratio,tv,tm,tl", [(10, 0.25, -0.02, 0.3), (100, 0.1633, -0.02, 0.33333),
+                                            (1000, 0.2, -0.01, 0.33333), (100, 0.1633, -0.02, 0.4)])
+def test_library_density_bounds_match_oracle_piecewise(ratio, tv, tm, tl):
+    """Eq. 11 rows of Table 1 (liquid slope below 1/3: psi^2 never returns to 0,
+    so there is no upper bound) and one liquid slope above 1/3 (a finite root)."""
+    r1, r2 = O.piecewise_breakpoints(1.0, ratio, tv, tm, tl)
+    oeos = O.piecewise(tv, tm, tl, r1, r2)
+    orv, orl = O.coexistence(oeos)
+    rv, rl, rmax, rmid = L.lbm_eos_bounds(L.piecewise(tv, tm, tl, r1, r2))
+    assert rmax == pytest.approx(O.rho_max(oeos, 0.0, orl), rel=1e-12)
+    assert (rmax == np.finfo(np.float64).max) == (tl <= 1.0 / 3.0)
+    assert rmid == pytest.approx(0.5 * (orv + orl), rel=1e-12)
+
+
 def test_invalid_eos_rejected():
     with pytest.raises(L.LbmError) as e:
         L.lbm_coexistence(L.carnahan_starling(), 1.0)  # above T_c
