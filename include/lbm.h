@@ -300,9 +300,14 @@ int lbm_mass_noalloc(const void *f, int nx, int ny, int precision, int walls, do
  * angles (theta per wall node, through sin(pi/2 - theta) of Eqs. 20-21 or
  * tan(pi/2 - theta) of Eq. 19) and the EOS temperature T, by the reverse-time
  * (adjoint) of the step, with the initial state held fixed.  The recorded
- * forward uses the canonical reference kernels (bit-identical to an FP64
- * evaluation of the step in that order at precision 64), whatever kernel
- * lbm_step uses.  Kinks: d sqrt(s)/ds = 0 at s = 0, d|a|/da = 0 at a = 0, a
+ * forward and the segment replays of the backward sweep run the context's own
+ * step kernel, so the recorded trajectory is the one lbm_step produces: at
+ * precision 64 the canonical reference kernels (bit-identical to an FP64
+ * evaluation of the step in that order), at precision 32 the fused kernel when
+ * the context uses it.  The reverse sweep transposes the canonical step at each
+ * recorded state, so in FP32 the gradient is the canonical step's transpose
+ * evaluated along the fused kernel's trajectory (the two steps differ by
+ * rounding only).  Kinks: d sqrt(s)/ds = 0 at s = 0, d|a|/da = 0 at a = 0, a
  * clamped ghost density passes no gradient.
  *
  * lbm_adjoint_record: advance the context by nsteps from its current state,
