@@ -101,9 +101,14 @@ typedef struct lbm_params {
                         with p(rho) = rho/3 (psi^2 >= 0 below it) */
   double rho_ghost_max; /* upper clamp of the Eqs. 19-21 ghost densities
                         (lower clamp 0); 0 means rho_max */
-  int graph_steps;   /* lbm_step replays this many steps (rounded up to even) as
-                        one captured CUDA graph while at least that many remain,
-                        when the context has a non-NULL stream; 0 = one launch
+  int graph_steps;   /* when the context has a non-NULL stream, lbm_step
+                        replays captured CUDA graphs: of this many steps
+                        (rounded up to even) while at least that many remain,
+                        then of the powers of two below it, largest first, so
+                        that at most one step of a call runs as a direct launch.
+                        All of them are captured by the first lbm_step of two or
+                        more steps, for both state arrays (call it before any
+                        capture of the context's stream).  0 = one launch
                         sequence per step.  Results are the same either way. */
 } lbm_params;
 
@@ -206,9 +211,9 @@ int lbm_step(lbm_ctx *ctx, int nsteps);
 /* Synchronise and read the device stability flag: LBM_OK or LBM_EUNSTABLE. */
 int lbm_status(lbm_ctx *ctx);
 
-/* Density at every node (nx*ny doubles): sum_a f_a at fluid nodes, the
- * ghost densities of the last step's wall rule on the solid rows (0 before
- * any step, and 0 for Martys-Chen). */
+/* Density at every node (nx*ny doubles): sum_a f_a (summed in double) at
+ * fluid nodes, 0 on the solid rows.  The ghost densities that the wall rule
+ * gives the solid rows for the current state come from lbm_get_fields. */
 int lbm_get_rho(lbm_ctx *ctx, double *rho);
 
 /* Velocity u = (sum_a f_a e_a + F/2)/rho (the half-force shifted velocity of
@@ -424,6 +429,14 @@ int lbm_batch_set_config(lbm_batch *b, const lbm_batch_config *cfg);
 int lbm_batch_get_plan(const lbm_batch *b, int *grid, int *items, int *smem_bytes, int *ctas_per_sm);
 /* Kernel launches issued by lbm_batch_step so far (graph replays included). */
 unsigned long long lbm_batch_launch_count(const lbm_batch *b);
+/* Fluid-node updates the batched kernel has computed for each instance since
+ * lbm_batch_create, into updates[lbm_batch_size(b)] (host): one per fluid node
+ * and step while the instance is stable.  An instance flagged unstable is
+ * frozen -- its remaining steps are skipped, not computed -- so its count
+ * stops at (about) the step where the flag was raised; lbm_batch_autotune's
+ * trials are not counted.  Throughput = the change of the sum over a timed
+ * interval / its duration.  Synchronises the batch's stream. */
+int lbm_batch_node_updates(lbm_batch *b, unsigned long long *updates);
 void lbm_batch_destroy(lbm_batch *b);
 
 #ifdef __cplusplus

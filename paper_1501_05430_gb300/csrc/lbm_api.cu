@@ -260,8 +260,8 @@ int graph_steps(const lbm_ctx *C) {
   return g + (g & 1);
 }
 
-// Capture G steps starting from array C->cur into an executable graph.
-int capture_steps(lbm_ctx *C, int G, cudaGraphExec_t *out) {
+// Capture G steps starting from array `start` into an executable graph.
+int capture_steps(lbm_ctx *C, int start, int G, cudaGraphExec_t *out) {
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
@@ -269,7 +269,7 @@ int capture_steps(lbm_ctx *C, int G, cudaGraphExec_t *out) {
   }
   unsigned long long dummy = 0;
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < G && e == cudaSuccess; ++k) e = launch_step(C, C->cur ^ (k & 1), &dummy);
+  for (int k = 0; k < G && e == cudaSuccess; ++k) e = launch_step(C, start ^ (k & 1), &dummy);
   cudaError_t e2 = cudaStreamEndCapture(C->stream, &graph);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
@@ -279,6 +279,27 @@ int capture_steps(lbm_ctx *C, int G, cudaGraphExec_t *out) {
     *out = nullptr;
     return LBM_ECUDA;
   }
+  return LBM_OK;
+}
+
+// The graph lengths of a context and their executable graphs for both
+// starting arrays (captured once; capture only records launches).
+int ensure_graphs(lbm_ctx *C, int G) {
+  if (C->graphs_ready) return LBM_OK;
+  int n = 0;
+  C->graph_len[n++] = G;
+  int p2 = 1;
+  while (p2 * 2 < G && p2 < (1 << 30)) p2 *= 2;
+  for (; p2 >= 2 && n < lbm_ctx::kMaxGraphs; p2 /= 2)
+    if (p2 < G) C->graph_len[n++] = p2;
+  C->ngraph = n;
+  for (int start = 0; start < 2; ++start)
+    for (int k = 0; k < n; ++k) {
+      if (C->step_graph[start][k]) continue;  // kept from an interrupted earlier attempt
+      int st = capture_steps(C, start, C->graph_len[k], &C->step_graph[start][k]);
+      if (st) return st;
+    }
+  C->graphs_ready = 1;
   return LBM_OK;
 }
 
@@ -379,7 +400,7 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
   C->red_len = 1024;
   bool ok = cudaMalloc(&C->d_coef, 4 * (size_t)nx * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&C->d_dcoef, 4 * (size_t)nx * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&C->d_flag, 2 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&C->d_flag, 4 * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&C->d_rho64, n * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&C->d_red, C->red_len * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&C->d_res, 16 * sizeof(double)) == cudaSuccess;
@@ -412,7 +433,7 @@ int create_impl(int nx, int ny, const lbm_eos *eos, double T, double tau, const 
     e1 = cudaMemcpy(C->d_dcoef, dcoef, 4 * (size_t)nx * sizeof(double), cudaMemcpyHostToDevice);
   free(coef);
   if (e1 != cudaSuccess || cudaMemsetAsync(C->state, 0, need, C->stream) != cudaSuccess ||
-      cudaMemsetAsync(C->d_flag, 0, 2 * sizeof(int), C->stream) != cudaSuccess) {
+      cudaMemsetAsync(C->d_flag, 0, 4 * sizeof(int), C->stream) != cudaSuccess) {
     cudaGetLastError();
     lbm_destroy(C);
     return LBM_ECUDA;
@@ -511,14 +532,15 @@ int lbm_create_with_buffer(int nx, int ny, const lbm_eos *eos, double T, double 
 int lbm_set_rho(lbm_ctx *C, const double *rho) {
   if (!C || !rho) return LBM_EINVAL;
   if (C->status) return C->status;
-  for (int y = 0; y < C->ny; ++y) {
-    if (C->walls && (y == 0 || y == C->ny - 1)) continue;
-    for (int x = 0; x < C->nx; ++x) {
-      double r = rho[(size_t)y * C->nx + x];
-      if (!(r > 0.0) || !isfinite(r)) return LBM_EINVAL;
-    }
-  }
+  // upload, check every fluid density on the device (finite and > 0), and only
+  // then overwrite the state
   CK(cudaMemcpyAsync(C->d_rho64, rho, n_nodes(C) * sizeof(double), cudaMemcpyHostToDevice, C->stream));
+  CK(cudaMemsetAsync(C->d_flag + 2, 0, sizeof(int), C->stream));
+  CK(lbm_ref_check_rho(C, C->d_rho64, C->d_flag + 2, &C->launches));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, C->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, C->stream));
+  CK(cudaStreamSynchronize(C->stream));
+  if (bad) return LBM_EINVAL;
   CK(lbm_ref_set_rho(C, C->d_rho64, C->f[C->cur], &C->launches));
   CK(cudaStreamSynchronize(C->stream));
   return LBM_OK;
@@ -553,23 +575,24 @@ int lbm_step(lbm_ctx *C, int nsteps) {
   if (C->status) return C->status;
   const int G = graph_steps(C);
   int it = 0;
-  if (G > 0) {
-    // whole graphs of G (even) steps: each replay starts and ends on the same array
-    while (nsteps - it >= G) {
-      cudaGraphExec_t &g = C->step_graph[C->cur];
-      if (!g) {
-        int st = capture_steps(C, G, &g);
-        if (st) return st;
-      }
-      CK(cudaGraphLaunch(g, C->stream));
-      C->launches += (unsigned long long)G * launches_per_step(C);
-      const long long before = C->steps;
-      C->steps += G;
-      it += G;
-      const int ce = C->params.check_every;
-      if (ce > 0 && C->steps / ce != before / ce) {
-        int st = read_flags(C);
-        if (st) return st;
+  if (G > 0 && nsteps >= 2) {
+    int st = ensure_graphs(C, G);
+    if (st) return st;
+    // whole graphs, longest first (even lengths: each replay starts and ends
+    // on the same array); at most one step is left for a direct launch
+    for (int k = 0; k < C->ngraph; ++k) {
+      const int len = C->graph_len[k];
+      while (nsteps - it >= len) {
+        CK(cudaGraphLaunch(C->step_graph[C->cur][k], C->stream));
+        C->launches += (unsigned long long)len * launches_per_step(C);
+        const long long before = C->steps;
+        C->steps += len;
+        it += len;
+        const int ce = C->params.check_every;
+        if (ce > 0 && C->steps / ce != before / ce) {
+          st = read_flags(C);
+          if (st) return st;
+        }
       }
     }
   }
@@ -790,7 +813,8 @@ void lbm_destroy(lbm_ctx *C) {
   if (!C) return;
   cudaStreamSynchronize(C->stream);
   for (int p = 0; p < 2; ++p)
-    if (C->step_graph[p]) cudaGraphExecDestroy(C->step_graph[p]);
+    for (int k = 0; k < lbm_ctx::kMaxGraphs; ++k)
+      if (C->step_graph[p][k]) cudaGraphExecDestroy(C->step_graph[p][k]);
   lbm_adjoint_free_tape(C);
   if (C->owns_state && C->state) cudaFree(C->state);
   if (C->d_coef) cudaFree(C->d_coef);

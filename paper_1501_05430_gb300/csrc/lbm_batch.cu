@@ -84,6 +84,7 @@ struct BatchArgs {
   unsigned *next;
   int *abort;              // [0]: a barrier wait ran out
   int *iflag;              // [ninst] bit 0 unstable, bit 1 timeout
+  unsigned long long *work;  // [ninst] fluid-node updates computed (frozen instances add none)
   const int *cur;          // [ninst] array index holding the state at phase 0
   int steps, phase;        // steps in this launch; parity of its first step
   int nxs, stages;         // stage row stride (floats), ring depth
@@ -457,6 +458,8 @@ __global__ void __launch_bounds__(kNT, 3) k_batch(BatchArgs A) {
       if (!ok) s_timeout = 1;
     }
     if (bad) s_bad = 1;
+    if (tid == 0 && !s_skip)
+      atomicAdd(A.work + it.inst, (unsigned long long)(it.y1 - it.y0) * (unsigned long long)sP.nx);
     __syncthreads();  // every store of the item issued; shared state free for the next entry
     if (s_timeout) {
       if (tid == 0) {
@@ -520,6 +523,7 @@ struct lbm_batch {
   unsigned *d_bar;            // [n] arrival counters + [1] work counter
   int *d_abort;
   int *d_iflag;
+  unsigned long long *d_work;  // [n] fluid-node updates computed per instance
   int *d_cur;
   size_t d_items_cap;
   int grid, nxs, smem, occ, nsm;
@@ -634,6 +638,7 @@ int launch(lbm_batch *B, int steps, int phase) {
   A.next = B->d_bar + B->n;
   A.abort = B->d_abort;
   A.iflag = B->d_iflag;
+  A.work = B->d_work;
   A.cur = B->d_cur;
   A.steps = steps;
   A.phase = phase;
@@ -817,6 +822,7 @@ int lbm_batch_create(int n, const lbm_instance_desc *inst, const lbm_batch_confi
             cudaMalloc(&B->d_bar, (size_t)(n + 1) * sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc(&B->d_abort, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&B->d_iflag, (size_t)n * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&B->d_work, (size_t)n * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&B->d_cur, (size_t)n * sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -826,6 +832,7 @@ int lbm_batch_create(int n, const lbm_instance_desc *inst, const lbm_batch_confi
   for (int i = 0; i < n; ++i) fill_inst(B->hinst[i], B->ctx[i], B->ctx[i]->d_flag);
   if (cudaMemsetAsync(B->d_abort, 0, sizeof(int), B->stream) != cudaSuccess ||
       cudaMemsetAsync(B->d_iflag, 0, (size_t)n * sizeof(int), B->stream) != cudaSuccess ||
+      cudaMemsetAsync(B->d_work, 0, (size_t)n * sizeof(unsigned long long), B->stream) != cudaSuccess ||
       cudaMemsetAsync(B->d_cur, 0, (size_t)n * sizeof(int), B->stream) != cudaSuccess) {
     cudaGetLastError();
     lbm_batch_destroy(B);
@@ -928,7 +935,11 @@ int lbm_batch_autotune(lbm_batch *B, int trial_steps, lbm_batch_config *best) {
   std::vector<int> cur0(B->n);
   for (int i = 0; i < B->n; ++i) cur0[i] = B->ctx[i]->cur;
   const int phase0 = B->phase;
-  cudaError_t e = cudaMemcpyAsync(save, B->pool, B->pool_bytes, cudaMemcpyDeviceToDevice, B->stream);
+  std::vector<unsigned long long> work0(B->n);  // the trials' work is not the caller's
+  cudaError_t e = cudaMemcpyAsync(work0.data(), B->d_work, (size_t)B->n * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, B->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(save, B->pool, B->pool_bytes, cudaMemcpyDeviceToDevice, B->stream);
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -1011,6 +1022,8 @@ int lbm_batch_autotune(lbm_batch *B, int trial_steps, lbm_batch_config *best) {
   }
   if (cudaMemcpyAsync(B->pool, save, B->pool_bytes, cudaMemcpyDeviceToDevice, B->stream) != cudaSuccess ||
       cudaMemsetAsync(B->d_iflag, 0, (size_t)B->n * sizeof(int), B->stream) != cudaSuccess ||
+      cudaMemcpyAsync(B->d_work, work0.data(), (size_t)B->n * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                      B->stream) != cudaSuccess ||
       cudaStreamSynchronize(B->stream) != cudaSuccess) {
     cudaGetLastError();
     st = LBM_ECUDA;
@@ -1031,6 +1044,14 @@ int lbm_batch_autotune(lbm_batch *B, int trial_steps, lbm_batch_config *best) {
 }
 
 unsigned long long lbm_batch_launch_count(const lbm_batch *B) { return B ? B->launches : 0ULL; }
+
+int lbm_batch_node_updates(lbm_batch *B, unsigned long long *updates) {
+  if (!B || !updates) return LBM_EINVAL;
+  BCK(cudaMemcpyAsync(updates, B->d_work, (size_t)B->n * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                      B->stream));
+  BCK(cudaStreamSynchronize(B->stream));
+  return LBM_OK;
+}
 
 int lbm_batch_get_plan(const lbm_batch *B, int *grid, int *items, int *smem_bytes, int *ctas_per_sm) {
   if (!B) return LBM_EINVAL;
@@ -1054,6 +1075,7 @@ void lbm_batch_destroy(lbm_batch *B) {
   cudaFree(B->d_bar);
   cudaFree(B->d_abort);
   cudaFree(B->d_iflag);
+  cudaFree(B->d_work);
   cudaFree(B->d_cur);
   cudaGetLastError();
   delete B;

@@ -177,13 +177,23 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
   const size_t n = (size_t)P.nx * P.ny;
   const bool geo = P.wetting == LBM_WET_GEOMETRIC;
 
+  // Programmatic dependent launch: the next step's grid may be scheduled once
+  // every CTA of this one has started (all of them are resident: the grid is
+  // one wave), so its CTAs take the slots of this grid's first finishers and
+  // do their set-up there; before touching global memory every thread waits
+  // until the previous grid has completed and its stores are visible (a
+  // no-op for a launch without a programmatic dependency).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (tid == 0) {
     s_abort = 0;
     for (int s = 0; s < S; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tm_main) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tm_halo) : "memory");
   }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
 
   // ---- producer -------------------------------------------------------------
@@ -218,8 +228,6 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
     }
   };
   if (producer) {
-    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tm_main) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tm_halo) : "memory");
     ps.init(P, u0, u1);
     issue_until(S);
   }
@@ -599,13 +607,30 @@ FusedArgs fused_args(const lbm_ctx *C) {
   return P;
 }
 
+// Launched with programmatic stream serialisation (the kernel orders its own
+// global accesses after the previous grid with griddepcontrol.wait), so that
+// back-to-back steps overlap one grid's tail with the next grid's launch and
+// set-up; LBM_FUSED_PDL=0 turns it off.
 cudaError_t launch_fused(lbm_ctx *C, const CUtensorMap &tm, const CUtensorMap &th, const FusedArgs &P,
                          unsigned long long *launches) {
-  const dim3 grid(C->tile_blocks), block(NCONS);
-  if (C->fused_unit) k_fused<true, kNC><<<grid, block, C->fused_smem, C->stream>>>(tm, th, P);
-  else k_fused<false, kNC><<<grid, block, C->fused_smem, C->stream>>>(tm, th, P);
+  static const int pdl = [] {
+    const char *e = getenv("LBM_FUSED_PDL");
+    return e && atoi(e) == 0 ? 0 : 1;
+  }();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C->tile_blocks);
+  cfg.blockDim = dim3(NCONS);
+  cfg.dynamicSmemBytes = (size_t)C->fused_smem;
+  cfg.stream = C->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl;
+  cudaError_t e = C->fused_unit ? cudaLaunchKernelEx(&cfg, k_fused<true, kNC>, tm, th, P)
+                                : cudaLaunchKernelEx(&cfg, k_fused<false, kNC>, tm, th, P);
   ++*launches;
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace

@@ -59,7 +59,7 @@ struct lbm_ctx {
   double *d_coef;        // 4*nx: c_bot, c_top, cot_bot, cot_top
   double *d_dcoef;       // 4*nx: their derivatives in theta (adjoint)
   struct lbm_tape *tape; // adjoint record (lbm_adjoint.cu); NULL when none
-  int *d_flag;           // [0]: instability, [1]: timeout
+  int *d_flag;           // [0]: instability, [1]: timeout, [2]: lbm_set_rho input check
   double *d_rho64;       // nx*ny, measurement density
   void *d_fields;        // 3*nx*ny reals: rho, psi, U (reference kernels)
   double *d_aux;         // 7*nx*ny doubles for lbm_get_u / lbm_get_fields (lazy)
@@ -71,8 +71,14 @@ struct lbm_ctx {
   int fused_cols;            // columns per thread of the fused kernel
   int tile_w, tile_blocks, tile_stages, fused_smem;
   unsigned char tmaps[4][128];   // CUtensorMap for f[0], f[1]: main box, halo box
-  // lbm_step graphs: graph_steps steps captured once per starting array
-  cudaGraphExec_t step_graph[2];
+  // lbm_step graphs, captured at the first lbm_step for both starting arrays:
+  // graph_len[0] = graph_steps (even), then every power of two 2 <= 2^k below
+  // it, largest first, so that any step count replays as whole graphs plus at
+  // most one direct launch
+  static constexpr int kMaxGraphs = 17;
+  int ngraph, graphs_ready;
+  int graph_len[kMaxGraphs];
+  cudaGraphExec_t step_graph[2][kMaxGraphs];
 };
 
 // ---- lbm_ref.cu: unfused kernels in the canonical evaluation order --------
@@ -84,6 +90,8 @@ cudaError_t lbm_ref_collide(const lbm_ctx *C, const void *fin, void *fout, const
 cudaError_t lbm_ref_macro(const lbm_ctx *C, const void *f, const void *fields, double *out7,
                           unsigned long long *launches);
 cudaError_t lbm_ref_set_rho(const lbm_ctx *C, const double *rho, void *f, unsigned long long *launches);
+// *bad |= 1 if a fluid-node density is not finite or not > 0 (bad zeroed by the caller)
+cudaError_t lbm_ref_check_rho(const lbm_ctx *C, const double *rho, int *bad, unsigned long long *launches);
 cudaError_t lbm_ref_droplets(const lbm_ctx *C, int n, const double *drop, double width, double *rho,
                              unsigned long long *launches);
 

@@ -11,6 +11,8 @@
 // same step in one pass; these kernels also serve the macroscopic getters.
 #include <math.h>
 
+#include <algorithm>
+
 #include "lbm_internal.h"
 #include "lbm_ref_node.cuh"
 
@@ -235,6 +237,29 @@ cudaError_t lbm_ref_macro(const lbm_ctx *C, const void *f, const void *fields, d
     k_macro<double><<<nblk(n, 128), 128, 0, C->stream>>>(C->dp, (const double *)f, (const double *)fields, out7);
   else
     k_macro<float><<<nblk(n, 128), 128, 0, C->stream>>>(C->dp, (const float *)f, (const float *)fields, out7);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+// Input check of lbm_set_rho: every fluid-node density finite and > 0.
+static __global__ void k_check_rho(int nx, int ny, int walls, const double *__restrict__ rho, int *bad) {
+  const size_t n = (size_t)nx * ny;
+  const size_t lo = walls ? (size_t)nx : 0, hi = walls ? n - nx : n;
+  int b = 0;
+  for (size_t i = lo + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (size_t)gridDim.x * blockDim.x) {
+    const double r = rho[i];
+    b |= !(r > 0.0) || !isfinite(r);
+  }
+  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
+cudaError_t lbm_ref_check_rho(const lbm_ctx *C, const double *rho, int *bad, unsigned long long *launches) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t n = (size_t)C->nx * C->ny;
+  const int blocks = (int)std::min<size_t>(nblk(n, 256), (size_t)std::max(1, nsm) * 8);
+  k_check_rho<<<blocks, 256, 0, C->stream>>>(C->nx, C->ny, C->walls, rho, bad);
   ++*launches;
   return cudaGetLastError();
 }

@@ -134,6 +134,7 @@ _SIGS = {
     "lbm_batch_get_plan": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                    ctypes.POINTER(c_int)]),
     "lbm_batch_launch_count": (ctypes.c_ulonglong, [c_void_p]),
+    "lbm_batch_node_updates": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
     "lbm_batch_destroy": (None, [c_void_p]),
 }
 
@@ -505,6 +506,14 @@ def lbm_batch_launch_count(b) -> int:
     return load().lbm_batch_launch_count(b)
 
 
+def lbm_batch_node_updates(b) -> np.ndarray:
+    n = lbm_batch_size(b)
+    out = np.zeros(n, dtype=np.uint64)
+    _check(load().lbm_batch_node_updates(b, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong))),
+           "lbm_batch_node_updates")
+    return out
+
+
 def lbm_batch_destroy(b):
     if b:
         load().lbm_batch_destroy(b)
@@ -653,6 +662,10 @@ class LbmBatch:
 
     def launches(self):
         return lbm_batch_launch_count(self.b)
+
+    def node_updates(self) -> np.ndarray:
+        """Fluid-node updates computed per instance (frozen instances stop counting)."""
+        return lbm_batch_node_updates(self.b)
 
     def close(self):
         if getattr(self, "b", None):

@@ -162,6 +162,14 @@ def test_unstable_instance_is_frozen_and_others_go_on():
         assert b[1].status() == L.LBM_EUNSTABLE
         for k in (0, 2, 3):
             assert np.array_equal(b[k].f(), ok[k].f())
+        # computed work: every fluid node of every step for the stable
+        # instances; the frozen one stops inside its first step (the NaN is
+        # found there; items of that step that start after the flag skip too)
+        upd = b.node_updates()
+        for k in (0, 2, 3):
+            assert upd[k] == cases[k].nx * (cases[k].ny - 2) * 9
+        assert 0 < upd[1] <= cases[1].nx * (cases[1].ny - 2)
+        assert upd[1] % cases[1].nx == 0
     _close(cases)
 
 
@@ -205,6 +213,10 @@ def test_autotune_keeps_the_state_and_installs_a_valid_shape():
         ref.step(5)
         for x, y in zip(b.instances, ref.instances):
             assert np.array_equal(x.f(), y.f())
+        # the trials' steps are not counted as the caller's work
+        want = np.array([c.nx * (c.ny - 2) * 8 for c in cases], dtype=np.uint64)
+        assert np.array_equal(b.node_updates(), want)
+        assert np.array_equal(ref.node_updates(), want)
     _close(cases)
 
 

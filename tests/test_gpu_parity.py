@@ -228,13 +228,21 @@ def _cap(nx, ny, R, theta, rv, rl, wall=0, xc=None):
 @pytest.mark.parametrize("theta_deg", [30, 90, 150])
 @pytest.mark.parametrize("wall", [0, 1])
 def test_contact_angle_matches_oracle_measurement(theta_deg, wall):
-    p = Pair(240, 200, precision=64, kernel=REF)
+    # the measurement kernel's arithmetic bit for bit: both sides interpolate
+    # the same contour (the oracle's rho_mid), then the library's own contour
+    p = Pair(240, 200, precision=64, kernel=REF, oracle_bounds=True)
     rho = _cap(240, 200, 40.0, math.radians(theta_deg), p.rho_v, p.rho_l, wall)
     p.set_rho(rho)
     th, H, L_ = p.gpu.contact_angle(wall, 20, 220)
     assert np.array_equal(p.gpu.rho(), p.orc.rho())
     ot, oH, oL, _ = O.contact_angle_field(p.orc.rho(), wall, 20, 220, p.rho_mid)
     assert th == pytest.approx(ot, rel=1e-13) and H == oH and L_ == oL
+    with L.Lbm(240, 200, p.geos, p.T, p.tau, params=L.lbm_params_default(precision=64), torch_state=False) as own:
+        assert own.info.rho_mid == pytest.approx(p.rho_mid, rel=1e-12)
+        own.set_rho(rho)
+        th2, H2, L2 = own.contact_angle(wall, 20, 220)
+        assert th2 == pytest.approx(ot, rel=1e-10) and H2 == pytest.approx(oH, rel=1e-10)
+        assert L2 == pytest.approx(oL, rel=1e-10)
     assert abs(math.degrees(th) - theta_deg) < 0.6
     with pytest.raises(L.LbmError) as e:
         p.gpu.contact_angle(wall, 0, 30)
@@ -309,9 +317,16 @@ def test_invalid_arguments():
     assert e.value.status == L.LBM_EUNSUPPORTED
     ctx = L.lbm_create(16, 10, eos, T, 1.0)
     rho = np.full((10, 16), 0.2)
-    rho[4, 4] = -1.0
-    with pytest.raises(L.LbmError):
-        L.lbm_set_rho(ctx, rho)
+    rho[0, 3] = rho[9, 5] = -1.0  # wall rows are ignored
+    L.lbm_set_rho(ctx, rho)
+    f0 = L.lbm_get_f(ctx)
+    for bad in (-1.0, 0.0, np.nan, np.inf):
+        r = rho.copy()
+        r[4, 4] = bad
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_set_rho(ctx, r)  # checked on the device before the state is touched
+        assert e.value.status == L.LBM_EINVAL
+        assert np.array_equal(L.lbm_get_f(ctx), f0)
     L.lbm_destroy(ctx)
 
 
