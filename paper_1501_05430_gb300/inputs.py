@@ -106,6 +106,12 @@ class Workload:
 # with pseudo-potential MRT models at large density ratios.  With all rates
 # equal to 1/tau (BGK) these cases blow up within 100 steps.
 LOW_T_RATES = dict(s_e=0.8, s_eps=0.8, s_j=1.0, s_q=1.1)
+# MRT rates for Carnahan-Starling at T/Tc = 0.5 (density ratio 724) with tau = 0.6:
+# smaller energy and energy-square rates (a larger bulk viscosity, which damps
+# the acoustic waves of the interfaces).  Measured on the 4096 x 2048 layout:
+# LOW_T_RATES blow up within 500-2000 steps, all rates 1 (except s_nu) within
+# 100, these run 5000 steps.
+RATIO_724_RATES = dict(s_e=0.6, s_eps=0.6, s_j=1.0, s_q=1.1)
 
 
 def plain_fp64() -> Workload:
@@ -134,26 +140,29 @@ def _cap_base(r0: float, theta_deg: float) -> float:
     return 2.0 * R * np.sin(t) if t <= 0.5 * np.pi else 2.0 * R
 
 
-def throughput(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: int = 12) -> Workload:
-    """Large density ratio: the Eq. 11 EOS of Table 1 at ratio 1000 with the
-    paper's relaxation (all rates 1, tau = 1), A = -0.6, kappa = 0.5, tanh
-    interfaces of width 10, theta ~ U[30, 150] deg per droplet, radii drawn
-    from U[40, 120].
+def cap_droplet(xc: float, r0: float, theta_deg: float, wall: int, ny: int) -> Tuple[float, float, float]:
+    """(xc, R, yc) of the 2-D circular cap at angle theta whose area equals a
+    semicircle of radius r0 on the bottom (wall 0) or top (wall 1) boundary
+    row, in the droplet_field form with an explicit centre row."""
+    t = np.deg2rad(theta_deg)
+    R = r0 * np.sqrt(0.5 * np.pi / (t - np.sin(t) * np.cos(t)))
+    yc = 1.0 - R * np.cos(t) if wall == 0 else (ny - 2.0) + R * np.cos(t)
+    return (float(xc), float(R), float(yc))
 
-    Each droplet gets a wall slot as wide as the base of the cap it relaxes to
-    at its angle (same area as the initial semicircle) plus a margin, and all
-    radii are scaled by one common factor so that the slots fill the wall;
-    theta is constant on each slot.  12 droplets per wall (24 in all): with 32
-    per wall (64) the slots are too narrow at ratio 1000 and the run blows up
-    within a few hundred steps; 16 per wall lasts about 4900 steps, 12 per
-    wall the full 5000."""
-    rng = np.random.default_rng(seed)
-    width = 10.0
+
+def _wall_layout(rng, nx: int, per_wall: int, width: float):
+    """Seeded droplets on both walls: radii from U[40, 120], theta from
+    U[30, 150] deg; each droplet gets a wall slot as wide as the base of the cap
+    it relaxes to at its angle (same area as the initial semicircle) plus a
+    margin, all radii scaled by one common factor so that the slots fill the
+    wall, theta constant on each slot.  Returns (droplets, bottom, top, regions,
+    theta_set, scales, per_wall) with per_wall lowered where the wall is too
+    short for it."""
     margin = 8.0 + 2.0 * width
-    droplets, regions, theta_set = [], [], []
+    per_wall = max(1, min(per_wall, int(nx // (margin + 20.0))))
+    droplets, regions, theta_set, scales = [], [], [], []
     bottom = np.full(nx, np.pi / 2)
     top = np.full(nx, np.pi / 2)
-    scales = []
     for wall in (0, 1):
         r = rng.uniform(40.0, 120.0, per_wall)
         th = rng.uniform(30.0, 150.0, per_wall)
@@ -173,10 +182,45 @@ def throughput(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: int =
             regions.append((wall, a, b))
             theta_set.append(float(th[k]))
             x0 = hi
-    return Workload(f"throughput_{nx}x{ny}_{2 * per_wall}drops_ratio1000", nx, ny, 0.0, 1.0, 5000, droplets,
+    return droplets, bottom, top, regions, theta_set, scales, per_wall
+
+
+def throughput(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: int = 12) -> Workload:
+    """Large density ratio with the paper's own model: the Eq. 11 EOS of
+    Table 1 at ratio 1000 with the paper's relaxation (all rates 1, tau = 1),
+    A = -0.6, kappa = 0.5, tanh interfaces of width 10, theta ~ U[30, 150] deg
+    per droplet, radii drawn from U[40, 120] (see _wall_layout).
+
+    12 droplets per wall (24 in all): with 32 per wall (64) the slots are too
+    narrow at ratio 1000 and the run blows up within a few hundred steps; 16
+    per wall lasts about 4900 steps, 12 per wall the full 5000."""
+    rng = np.random.default_rng(seed)
+    width = 10.0
+    droplets, bottom, top, regions, theta_set, scales, pw = _wall_layout(rng, nx, per_wall, width)
+    return Workload(f"throughput_{nx}x{ny}_{2 * pw}drops_ratio1000", nx, ny, 0.0, 1.0, 5000, droplets,
                     theta_field(nx, ny, bottom, top), regions, theta_set, {}, width=width,
                     eos=table1_eos(1000),
                     notes=f"radius scale factors per wall {scales[0]:.4f}, {scales[1]:.4f}")
+
+
+def throughput_cs(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: int = 12) -> Workload:
+    """Large density ratio with the Carnahan-Starling EOS: T/Tc = 0.5 (density
+    ratio 724), tau = 0.6 with the MRT rates of RATIO_724_RATES (so the fused
+    kernel runs its general-rate collision), A = -0.6, kappa = 0.5, the wall
+    layout of ``throughput`` (same seed: same radii, angles and slots), each
+    droplet started as the circular cap at its angle with the area of its
+    semicircle, tanh interfaces of width 10.  a = 0.25 (the coexistence
+    densities depend only on b and T/Tc; with a = 1 the liquid's dp/drho
+    exceeds c_s^2 and every run blows up within 500 steps)."""
+    rng = np.random.default_rng(seed)
+    width = 10.0
+    droplets, bottom, top, regions, theta_set, scales, pw = _wall_layout(rng, nx, per_wall, width)
+    caps = [cap_droplet(xc, r, th, wall, ny) for (xc, r, wall), th in zip(droplets, theta_set)]
+    return Workload(f"throughput_cs_{nx}x{ny}_{2 * pw}drops_T0.5", nx, ny, 0.5, 0.6, 5000, caps,
+                    theta_field(nx, ny, bottom, top), regions, theta_set, dict(RATIO_724_RATES), width=width,
+                    eos=cs_eos(a=0.25),
+                    notes=f"radius scale factors per wall {scales[0]:.4f}, {scales[1]:.4f}; caps of the "
+                          f"semicircles' areas")
 
 
 def batched(seed: int = 42, count: int = 256, width: float = 3.0):
