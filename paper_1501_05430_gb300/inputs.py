@@ -8,8 +8,9 @@ Workloads (the paper gives no grid sizes; these follow its setup of
 Secs. 3.1 and 4.2 -- a semicircular droplet on the bottom wall -- at the
 sizes of the benchmark configurations):
   plain_fp64       100 x 60, CS T/Tc = 0.8, tau = 1, R0 = 20, theta = 90 deg
-  single_droplet   400 x 200, CS (a = 0.25) T/Tc = 0.6, tau = 0.8, R0 = 60
+  single_droplet   400 x 200, CS (a = 0.25) T/Tc = 0.6, tau = 0.8, R0 = 60, A = -0.9
   throughput       4096 x 2048, Table 1 EOS at ratio 1000, tau = 1, 12 droplets per wall
+  throughput_cs    4096 x 2048, CS (a = 0.25) T/Tc = 0.5, tau = 0.6, A = -0.9, same layout
   batched          256 instances of {128x64 .. 512x256}, seeded theta, T/Tc, tau
   adjoint_case     256 x 128, CS T/Tc = 0.7, tau = 1, R0 = 40, per-wall-node theta
 """
@@ -106,12 +107,14 @@ class Workload:
 # with pseudo-potential MRT models at large density ratios.  With all rates
 # equal to 1/tau (BGK) these cases blow up within 100 steps.
 LOW_T_RATES = dict(s_e=0.8, s_eps=0.8, s_j=1.0, s_q=1.1)
-# MRT rates for Carnahan-Starling at T/Tc = 0.5 (density ratio 724) with tau = 0.6:
-# smaller energy and energy-square rates (a larger bulk viscosity, which damps
-# the acoustic waves of the interfaces).  Measured on the 4096 x 2048 layout:
-# LOW_T_RATES blow up within 500-2000 steps, all rates 1 (except s_nu) within
-# 100, these run 5000 steps.
-RATIO_724_RATES = dict(s_e=0.6, s_eps=0.6, s_j=1.0, s_q=1.1)
+# Eq. 9 mixing parameter for the Carnahan-Starling workloads.  The paper's
+# A = -0.6 goes with its piecewise EOS (Table 1); with Carnahan-Starling it
+# leaves the flat-interface vapour far below the Maxwell density (T/Tc = 0.6:
+# 1.8e-5 against 3.1e-3) or without a vapour phase at all (T/Tc = 0.5: the
+# vapour condenses onto the liquid until a node reaches zero density).  At
+# A = -0.9 the method's flat-interface densities are Maxwell's within 11%
+# (vapour) and 0.1% (liquid) from T/Tc = 0.5 to 0.8 (a = 0.25, b = 4, R = 1).
+CS_A = -0.9
 
 
 def plain_fp64() -> Workload:
@@ -122,14 +125,16 @@ def plain_fp64() -> Workload:
 
 
 def single_droplet(theta_deg: float = 90.0) -> Workload:
-    """Carnahan-Starling at T/Tc = 0.6 (density ratio 132), tau = 0.8.  The
-    attraction is scaled to a = 0.25: with a = 1 the liquid has
-    dp/drho = 0.57 > c_s^2 = 1/3, psi(rho) falls through the liquid and angles
-    below 60 deg blow up; the coexistence densities do not depend on a."""
+    """Carnahan-Starling at T/Tc = 0.6 (density ratio 132), tau = 0.8, A = CS_A,
+    a droplet of radius 60 started as the circular cap at theta_deg with the
+    semicircle's area.  The attraction is scaled to a = 0.25: with a = 1 the
+    liquid has dp/drho = 0.57 > c_s^2 = 1/3, psi(rho) falls through the liquid
+    and angles below 60 deg blow up; the coexistence densities do not depend
+    on a."""
     nx, ny = 400, 200
     return Workload(f"single_droplet_400x200_theta{int(theta_deg)}", nx, ny, 0.6, 0.8, 20000,
-                    [(200.0, 60.0, 0)], theta_field(nx, ny, np.deg2rad(theta_deg), np.pi / 2),
-                    [(0, 0, nx)], [theta_deg], dict(LOW_T_RATES), eos=cs_eos(a=0.25))
+                    [cap_droplet(200.0, 60.0, theta_deg, 0, ny)], theta_field(nx, ny, np.deg2rad(theta_deg), np.pi / 2),
+                    [(0, 0, nx)], [theta_deg], dict(LOW_T_RATES), eos=cs_eos(a=0.25), A=CS_A)
 
 
 def _cap_base(r0: float, theta_deg: float) -> float:
@@ -205,8 +210,8 @@ def throughput(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: int =
 
 def throughput_cs(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: int = 12) -> Workload:
     """Large density ratio with the Carnahan-Starling EOS: T/Tc = 0.5 (density
-    ratio 724), tau = 0.6 with the MRT rates of RATIO_724_RATES (so the fused
-    kernel runs its general-rate collision), A = -0.6, kappa = 0.5, the wall
+    ratio 724), tau = 0.6 with the MRT rates of LOW_T_RATES (so the fused
+    kernel runs its general-rate collision), A = CS_A, kappa = 0.5, the wall
     layout of ``throughput`` (same seed: same radii, angles and slots), each
     droplet started as the circular cap at its angle with the area of its
     semicircle, tanh interfaces of width 10.  a = 0.25 (the coexistence
@@ -217,8 +222,8 @@ def throughput_cs(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: in
     droplets, bottom, top, regions, theta_set, scales, pw = _wall_layout(rng, nx, per_wall, width)
     caps = [cap_droplet(xc, r, th, wall, ny) for (xc, r, wall), th in zip(droplets, theta_set)]
     return Workload(f"throughput_cs_{nx}x{ny}_{2 * pw}drops_T0.5", nx, ny, 0.5, 0.6, 5000, caps,
-                    theta_field(nx, ny, bottom, top), regions, theta_set, dict(RATIO_724_RATES), width=width,
-                    eos=cs_eos(a=0.25),
+                    theta_field(nx, ny, bottom, top), regions, theta_set, dict(LOW_T_RATES), width=width,
+                    eos=cs_eos(a=0.25), A=CS_A,
                     notes=f"radius scale factors per wall {scales[0]:.4f}, {scales[1]:.4f}; caps of the "
                           f"semicircles' areas")
 
@@ -226,9 +231,12 @@ def throughput_cs(seed: int = 1234, nx: int = 4096, ny: int = 2048, per_wall: in
 def batched(seed: int = 42, count: int = 256, width: float = 3.0):
     """Independent droplet instances: size uniform over {128x64, 256x128,
     384x192, 512x256}, theta ~ U(20, 160) deg, T/Tc in {0.5, 0.6, 0.7, 0.8},
-    tau ~ U[0.6, 1.0], R0 = nx/4 centred on the bottom wall.  Carnahan-Starling
-    with a = 0.25 (the coexistence densities depend only on b and T/Tc) and the
-    low-temperature MRT rates below T/Tc = 0.7, as for single_droplet."""
+    tau ~ U[0.6, 1.0], a droplet of radius R0 = nx/4 on the bottom wall,
+    started as the circular cap at its angle with the area of the semicircle
+    of radius R0 (a semicircle far from its angle sheds its excess energy in a
+    transient that blows up 10 of the 256 at T/Tc = 0.5).  Carnahan-Starling with
+    a = 0.25 (the coexistence densities depend only on b and T/Tc), A = CS_A and
+    the low-temperature MRT rates below T/Tc = 0.7, as for single_droplet."""
     rng = np.random.default_rng(seed)
     sizes = [(128, 64), (256, 128), (384, 192), (512, 256)]
     out = []
@@ -237,9 +245,10 @@ def batched(seed: int = 42, count: int = 256, width: float = 3.0):
         th = rng.uniform(20.0, 160.0)
         tr = [0.5, 0.6, 0.7, 0.8][rng.integers(0, 4)]
         tau = rng.uniform(0.6, 1.0)
-        out.append(Workload(f"batch{i}_{nx}x{ny}", nx, ny, tr, tau, 10000, [(nx / 2.0, nx / 4.0, 0)],
+        out.append(Workload(f"batch{i}_{nx}x{ny}", nx, ny, tr, tau, 10000,
+                            [cap_droplet(nx / 2.0, nx / 4.0, th, 0, ny)],
                             theta_field(nx, ny, np.deg2rad(th)), [(0, 0, nx)], [th],
-                            dict(LOW_T_RATES) if tr < 0.7 else {}, width=width, eos=cs_eos(a=0.25)))
+                            dict(LOW_T_RATES) if tr < 0.7 else {}, width=width, eos=cs_eos(a=0.25), A=CS_A))
     return out
 
 

@@ -77,6 +77,36 @@ def test_throughput_layout(nx, ny):
         assert "1.0000, 1.0000" in w.notes and all(40.0 <= d[1] <= 120.0 for d in w.droplets)
 
 
+@pytest.mark.parametrize("wall", [0, 1])
+def test_cap_droplet_keeps_the_semicircle_area_and_meets_the_wall_at_theta(wall):
+    ny = 120
+    for deg in (20.0, 45.0, 90.0, 135.0, 160.0):
+        xc, R, yc = I.cap_droplet(50.0, 30.0, deg, wall, ny)
+        t = np.deg2rad(deg)
+        assert R * R * (t - np.sin(t) * np.cos(t)) == pytest.approx(0.5 * np.pi * 30.0 ** 2, rel=1e-12)
+        base = 1.0 if wall == 0 else ny - 2.0
+        # the circle crosses the boundary row with half-width R sin(theta), and its
+        # centre sits below (acute) or above (obtuse) the row for the bottom wall
+        h = abs(base - yc)
+        assert np.sqrt(R * R - h * h) == pytest.approx(R * np.sin(t), rel=1e-9)
+        if deg != 90.0:
+            assert ((yc < base) == (deg < 90.0)) if wall == 0 else ((yc > base) == (deg < 90.0))
+    assert I.cap_droplet(50.0, 30.0, 90.0, 0, ny) == pytest.approx((50.0, 30.0, 1.0))
+
+
+def test_throughput_cs_shares_the_layout():
+    a, b = I.throughput(), I.throughput_cs()
+    assert np.array_equal(a.theta, b.theta) and a.regions == b.regions and a.theta_set == b.theta_set
+    assert b.eos == I.cs_eos(a=0.25) and b.t_over_tc == 0.5 and b.tau == 0.6 and b.A == I.CS_A
+    assert b.rates == I.LOW_T_RATES and not _unit(b)
+    for (xc, r0, wall), (xc2, R, yc), th in zip(a.droplets, b.droplets, a.theta_set):
+        assert (xc2, R, yc) == I.cap_droplet(xc, r0, th, wall, b.ny)
+
+
+def _unit(w):
+    return w.tau == 1.0 and all(v in (0.0, 1.0) for v in w.rates.values())
+
+
 def test_cap_base_keeps_the_semicircle_area():
     r0 = 50.0
     for deg in (30.0, 60.0, 90.0, 120.0, 150.0):
@@ -99,9 +129,14 @@ def test_batched_recipe():
     for w in insts:
         assert 20.0 <= w.theta_set[0] <= 160.0 and np.allclose(w.theta[0], np.deg2rad(w.theta_set[0]))
         assert w.t_over_tc in (0.5, 0.6, 0.7, 0.8) and 0.6 <= w.tau <= 1.0
-        assert w.droplets == [(w.nx / 2.0, w.nx / 4.0, 0)]
+        # the cap at the instance's angle with the area of the semicircle of radius nx/4
+        xc, R, yc = w.droplets[0]
+        t = np.deg2rad(w.theta_set[0])
+        assert len(w.droplets) == 1 and xc == w.nx / 2.0
+        assert R * R * (t - np.sin(t) * np.cos(t)) == pytest.approx(0.5 * np.pi * (w.nx / 4.0) ** 2, rel=1e-12)
+        assert yc == pytest.approx(1.0 - R * np.cos(t), rel=1e-12)
         assert (w.rates == I.LOW_T_RATES) == (w.t_over_tc < 0.7)
-        assert w.eos == I.cs_eos(a=0.25)
+        assert w.eos == I.cs_eos(a=0.25) and w.A == I.CS_A == -0.9
 
 
 def test_adjoint_case():
