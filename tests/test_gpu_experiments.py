@@ -9,6 +9,8 @@ of paper_1501_05430_gb300.experiments, each run as one batched sweep:
   distorts the near-wall density (Figs. 1, 3), sets smaller angles for stronger
   attraction (Fig. 1), is unstable at ratio 1000 (Sec. 3.1), and its angle
   moves more with kappa than the geometric rule's (Figs. 4, 9)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -81,18 +83,40 @@ def test_martys_chen_distorts_the_near_wall_density(results):
     assert vap[0] > 2.0 * vap[12]
 
 
+E7E8_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "e7e8_oracle_angles.txt")
+
+
+def _e7e8_oracle():
+    """{(preset, theta_set): angle} of the FP64 oracle's preset runs (cap start,
+    four iterations, 30,000 steps), from make_e7e8_oracle_angles.py."""
+    out, cols = {}, None
+    for line in open(E7E8_GOLDEN):
+        if line.startswith("# tag"):
+            cols = line[2:].split()
+        elif line.strip() and not line.startswith("#"):
+            r = dict(zip(cols, line.split()))
+            if r["tag"] == "preset":
+                out[(r["preset"], float(r["theta"]))] = float(r["angle"])
+    return out
+
+
 @pytest.mark.parametrize("name", ["E7", "E8"])
 def test_geometric_rule_is_stable_over_15_to_150_degrees(results, name):
     """Figs. 6-7: every set angle in {15, ..., 150} runs stably at ratio 100
     and 1000 and keeps a contact line; the measured angle rises with the set
-    one and is within 3 deg of it up to 90 deg."""
+    one, is within 3 deg of it up to 90 deg, and at every angle -- the obtuse
+    ones included, where the four-iterate ghost rule and the droplet's
+    resolution put it 5-25 deg above the set value -- within 0.5 deg of the
+    FP64 oracle's angle for the same run."""
     res = results(name, init="cap")
+    ref = _e7e8_oracle()
     th = []
     for r in res:
         assert r["status"] == "stable" and r["contact"] == "cap", r
         th.append(r["theta"])
         if r["theta_set"] <= 90.0:
             assert abs(r["theta"] - r["theta_set"]) <= 3.0, r
+        assert abs(r["theta"] - ref[(name, r["theta_set"])]) <= 0.5, (r, ref[(name, r["theta_set"])])
     assert np.all(np.diff(th) > 0)
 
 
