@@ -48,6 +48,7 @@ namespace {
 using lbm_node::add2;
 using lbm_node::collide_node2;
 using lbm_node::eos_node;
+using lbm_node::eos_node2;
 using lbm_node::ghost_value;
 
 constexpr int kNT = 256;       // threads per CTA: thread t < nx/2 owns columns t and t + nx/2 (one lane pair)
@@ -60,9 +61,10 @@ constexpr int kMaxRing = 16;     // row slots (and mbarriers) of the copy ring a
 // kernel's) and the batch bookkeeping.
 struct BInst {
   int kind, wetting, walls, nx, ny, n_iter;
-  float b4, RT, a, r1, r2, pc0, pc1, pc2;
+  float b4, RT2, a2, r1, r2, pc0, pc1, pc2;
   float A, omA, pre, halfA, rho_max, ghost_max;
-  float se, seps, sq, snu, he, heps, hq, hnu, Gw;
+  lbm_node::RateK k;
+  float Gw;
   const double *coef;
   int unit;    // all non-conserved rates are 1
   int items;   // items of this instance = barrier arrivals per step
@@ -267,13 +269,13 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
                                    add2(add2(fin[4], fin[5]), add2(fin[6], fin[7]))),
                               fin[8]);
         rc = r;
-        const float4 e0 = eos_node(P, r.x);
-        put(pcur, qcur, c0, e0.y, e0.z);
+        float2 ps, ps2;
+        eos_node2(P, r, ps, ps2);
+        put(pcur, qcur, c0, ps.x, ps2.x);
         if (brow) putr(c0, r.x);
         bad |= !(r.x > 0.0f) || r.x > P.rho_max;
         if (act1) {
-          const float4 e1 = eos_node(P, r.y);
-          put(pcur, qcur, c1, e1.y, e1.z);
+          put(pcur, qcur, c1, ps.y, ps2.y);
           if (brow) putr(c1, r.y);
           bad |= !(r.y > 0.0f) || r.y > P.rho_max;
         }
@@ -698,8 +700,8 @@ void fill_inst(BInst &I, const lbm_ctx *C, int *flag) {
   I.ny = C->ny;
   I.n_iter = D.n_iter;
   I.b4 = (float)(0.25 * D.b);
-  I.RT = (float)(D.R * D.T);
-  I.a = (float)D.a;
+  I.RT2 = (float)(-2.0 * D.R * D.T);
+  I.a2 = (float)(2.0 * D.a);
   I.r1 = (float)D.r1;
   I.r2 = (float)D.r2;
   I.pc0 = (float)(-2.0 * (D.thv - 1.0 / 3.0));
@@ -711,14 +713,7 @@ void fill_inst(BInst &I, const lbm_ctx *C, int *flag) {
   I.halfA = (float)(0.5 * D.A);
   I.rho_max = (float)fmin(D.rho_max, 3.0e38);
   I.ghost_max = (float)fmin(D.ghost_max, 3.0e38);
-  I.se = (float)D.s[1];
-  I.seps = (float)D.s[2];
-  I.sq = (float)D.s[4];
-  I.snu = (float)D.s[7];
-  I.he = (float)(1.0 - 0.5 * D.s[1]);
-  I.heps = (float)(1.0 - 0.5 * D.s[2]);
-  I.hq = (float)(1.0 - 0.5 * D.s[4]);
-  I.hnu = (float)(1.0 - 0.5 * D.s[7]);
+  I.k = lbm_node::rate_consts(D.s);
   I.Gw = (float)D.Gw;
   I.coef = C->d_coef;
   I.unit = D.s[1] == 1.0 && D.s[2] == 1.0 && D.s[4] == 1.0 && D.s[7] == 1.0;

@@ -38,6 +38,7 @@ namespace {
 using lbm_node::add2;
 using lbm_node::collide_node2;
 using lbm_node::eos_node;
+using lbm_node::eos_node2;
 using lbm_node::ghost_node;
 using lbm_node::sqrt0;
 
@@ -64,11 +65,10 @@ struct FusedArgs {
   int nstrips, nrows, y0;
   long long total;
   int stages;
-  float b4, RT, a, r1, r2, pc0, pc1, pc2;      // EOS constants (b/4, R*T, a; Eq. 11 break-
+  float b4, RT2, a2, r1, r2, pc0, pc1, pc2;    // EOS constants (b/4, -2RT, 2a; Eq. 11 break-
                                                 // points and slopes folded into -2U)
   float A, omA, pre, halfA, rho_max, ghost_max; // force / Q constants, bounds
-  float se, seps, sq, snu;                      // rates
-  float he, heps, hq, hnu;                      // 1 - s/2
+  lbm_node::RateK k;                            // relaxation constants
   float Gw;
   const double *coef;
   float *fout;
@@ -295,14 +295,14 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         const float2 r = add2(add2(add2(add2(fin[0], fin[1]), add2(fin[2], fin[3])),
                                    add2(add2(fin[4], fin[5]), add2(fin[6], fin[7]))),
                               fin[8]);
-        const float4 e0 = eos_node(P, r.x);
+        float2 ps, ps2;
+        eos_node2(P, r, ps, ps2);
         rcur[c0 + 2] = r.x;
-        put(pcur, qcur, c0, e0.y, e0.z);
+        put(pcur, qcur, c0, ps.x, ps2.x);
         bad |= !(r.x > 0.0f) || r.x > P.rho_max;
         if (act1) {
-          const float4 e1 = eos_node(P, r.y);
           rcur[c1 + 2] = r.y;
-          put(pcur, qcur, c1, e1.y, e1.z);
+          put(pcur, qcur, c1, ps.y, ps2.y);
           bad |= !(r.y > 0.0f) || r.y > P.rho_max;
         }
       }
@@ -579,8 +579,8 @@ FusedArgs fused_args(const lbm_ctx *C) {
   P.total = (long long)P.nstrips * P.nrows;
   P.stages = C->tile_stages;
   P.b4 = (float)(0.25 * D.b);
-  P.RT = (float)(D.R * D.T);
-  P.a = (float)D.a;
+  P.RT2 = (float)(-2.0 * D.R * D.T);
+  P.a2 = (float)(2.0 * D.a);
   P.r1 = (float)D.r1;
   P.r2 = (float)D.r2;
   P.pc0 = (float)(-2.0 * (D.thv - 1.0 / 3.0));
@@ -592,14 +592,7 @@ FusedArgs fused_args(const lbm_ctx *C) {
   P.halfA = (float)(0.5 * D.A);
   P.rho_max = (float)fmin(D.rho_max, 3.0e38);
   P.ghost_max = (float)fmin(D.ghost_max, 3.0e38);
-  P.se = (float)D.s[1];
-  P.seps = (float)D.s[2];
-  P.sq = (float)D.s[4];
-  P.snu = (float)D.s[7];
-  P.he = (float)(1.0 - 0.5 * D.s[1]);
-  P.heps = (float)(1.0 - 0.5 * D.s[2]);
-  P.hq = (float)(1.0 - 0.5 * D.s[4]);
-  P.hnu = (float)(1.0 - 0.5 * D.s[7]);
+  P.k = lbm_node::rate_consts(D.s);
   P.Gw = (float)D.Gw;
   P.coef = C->d_coef;
   P.fout = nullptr;
