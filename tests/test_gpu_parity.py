@@ -126,13 +126,15 @@ def test_fp32_fused_single_droplet_1000_steps():
     p.close()
 
 
-@pytest.mark.parametrize("nx,ny", [(100, 40), (260, 24), (8, 9), (132, 7), (4, 5)])
+@pytest.mark.parametrize("nx,ny", [(100, 40), (260, 24), (8, 9), (132, 7), (4, 5), (800, 10)])
 @pytest.mark.parametrize("name", list(VARIANTS))
 def test_fp32_fused_variants(name, nx, ny):
     """Ragged strips (nx not a multiple of 128), tiny grids down to the
     smallest the library takes (4 x 5: one 4-column strip whose halo boxes
-    wrap onto itself) and every model variant: FP32 fused vs FP64 oracle after
-    12 steps."""
+    wrap onto itself), a strip away from the x wrap (800 wide: the middle
+    strip's interior rows take the single-address store path, in a walled and
+    a fully periodic box) and every model variant: FP32 fused vs FP64 oracle
+    after 12 steps."""
     p, walls = _variant_pair(name, nx, ny, 32, FUSED, seed=nx + ny)
     assert p.gpu.info.kernel_in_use == FUSED
     assert p.step(12) == 0
