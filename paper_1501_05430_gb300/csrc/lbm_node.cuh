@@ -118,11 +118,18 @@ __device__ __forceinline__ float4 ghost_node(const PT &P, const float *r1, const
 // The same node arithmetic on lane pairs (two nodes of one row that a thread
 // owns) with the packed FP32 instructions of sm_100+: one instruction issues
 // the operation for both nodes.  Each lane is an IEEE single-precision
-// operation; subtraction is fma(b, -1, a), which rounds like a - b.
+// operation.
 
 __device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.0f), a); }
+// a - b lane by lane (packed subtraction, rounded like the scalar a - b)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+  return *reinterpret_cast<float2 *>(&r);
+}
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
@@ -195,7 +202,6 @@ __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, cons
   const float2 v2 = fma2(vx, vx, mul2(vy, vy));
   const float2 vF = fma2(vx, Fx, mul2(vy, Fy));
   const float2 sQ = add2(Qxx, Qyy), dQ = sub2(Qxx, Qyy);
-  const float2 mone = bc2(-1.0f);
   // r_k = m*_k / N_k of the non-conserved moments (constants of RateK)
   float2 r1, r2, r4, r6, r7, r8;
   if (UNIT) {
@@ -206,15 +212,15 @@ __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, cons
     r4 = fma2(bc2(-1.0f / 12.0f), rvx, mul2(bc2(-1.0f / 24.0f), Fx));
     r6 = fma2(bc2(-1.0f / 12.0f), rvy, mul2(bc2(-1.0f / 24.0f), Fy));
     // (rvx vx - rvy vy + vx Fx - vy Fy - (Qxx - Qyy)) / 4
-    r7 = mul2(bc2(0.25f), fma2(vx, add2(rvx, Fx), mul2(mone, fma2(vy, add2(rvy, Fy), dQ))));
+    r7 = mul2(bc2(0.25f), sub2(mul2(vx, add2(rvx, Fx)), fma2(vy, add2(rvy, Fy), dQ)));
     // (rvx vy + (vx Fy + vy Fx)/2 - Qxy) / 4
-    r8 = fma2(bc2(0.25f), fma2(rvx, vy, mul2(mone, Qxy)), mul2(bc2(0.125f), fma2(vx, Fy, mul2(vy, Fx))));
+    r8 = fma2(bc2(0.25f), sub2(mul2(rvx, vy), Qxy), mul2(bc2(0.125f), fma2(vx, Fy, mul2(vy, Fx))));
   } else {
     const lbm_node::RateK &K = P.k;
     // non-conserved moments of f (rows e, eps, qx, qy, pxx, pxy of M)
     const float2 a13 = add2(f[1], f[3]), a24 = add2(f[2], f[4]);
     const float2 ax = add2(a13, a24), dg = add2(add2(f[5], f[6]), add2(f[7], f[8]));
-    const float2 me = fma2(bc2(-4.0f), f[0], fma2(bc2(2.0f), dg, mul2(mone, ax)));
+    const float2 me = sub2(mul2(bc2(2.0f), dg), fma2(bc2(4.0f), f[0], ax));
     const float2 meps = fma2(bc2(4.0f), f[0], fma2(m2, ax, dg));
     const float2 mqx = fma2(m2, s13, add2(d57, d86));
     const float2 mqy = fma2(m2, s24, sub2(d57, d86));
@@ -230,7 +236,7 @@ __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, cons
     // n_e (rvx vx - rvy vy) + n_F2 (vx Fx - vy Fy) = vx (n_e rvx + n_F2 Fx) - vy (n_e rvy + n_F2 Fy)
     const float2 ax7 = fma2(bc2(K.n_e), rvx, mul2(bc2(K.n_F2), Fx));
     const float2 ay7 = fma2(bc2(K.n_e), rvy, mul2(bc2(K.n_F2), Fy));
-    r7 = fma2(bc2(K.n_m), mpxx, fma2(vx, ax7, fma2(mul2(mone, vy), ay7, mul2(bc2(K.n_Q), dQ))));
+    r7 = fma2(bc2(K.n_m), mpxx, fma2(vx, ax7, sub2(mul2(bc2(K.n_Q), dQ), mul2(vy, ay7))));
     r8 = fma2(bc2(K.n_m), mpxy, fma2(mul2(bc2(K.n_e), rvx), vy,
                                      fma2(bc2(K.n_F1), fma2(vx, Fy, mul2(vy, Fx)), mul2(bc2(K.n_Q), Qxy))));
   }
