@@ -174,6 +174,9 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "c5_oracle_fd.txt")
 
 
 def _golden():
+    """(meta, h_target, rows); a row is (name, index, fd, err, fd_coarse): the
+    central difference at the middle rung of a step ladder, its noise estimate
+    (largest change to the neighbouring rungs) and the one at the coarsest."""
     meta, rows, h_t = {}, [], None
     lines = open(GOLDEN).read().splitlines()
     for k, line in enumerate(lines):
@@ -185,15 +188,38 @@ def _golden():
         elif line.startswith("# h_target"):
             h_t = np.array([float(v) for v in lines[k + 1][2:].split()])
         elif not line.startswith("#") and line.strip():
-            name, idx, g = line.split()
-            rows.append((name, int(idx), float(g)))
+            name, idx, fd, err, coarse = line.split()
+            rows.append((name, int(idx), float(fd), float(err), float(coarse)))
     return meta, h_t, rows
 
 
+# Tolerances.  FP64: 1e-3 relative on every row (measured: <= 7e-6).  FP32:
+# the gradient is the canonical step's transpose evaluated along the FP32
+# trajectory, whose densities differ from the FP64 ones by ~1e-4 relative per
+# 1000 steps, so on a wall angle where the loss is smooth it moves by a few
+# 1e-4 (measured: 1e-4 .. 5.4e-4).  Next to a ghost-clamp kink the FP32
+# trajectory switches the clamp at slightly different parameter values, and
+# the derivative moves by up to the slope change across the kinks, which the
+# step ladder measures as |fd(1e-4) - fd| / |fd| (theta_169: 5.5e-3; its FP32
+# gradient is 1.5e-3 .. 2.2e-3 off).  A wall angle is therefore held to
+# 1e-3 + that kink term.  dL/dT sums the EOS sensitivity of every node in every
+# step, so its FP32 rounding accumulates over 32768 nodes x 2000 steps
+# (measured 7e-4 .. 1.2e-3): held to 3e-3.
+def _tol(precision, name, fd, coarse):
+    if precision == 64:
+        return 1e-3
+    if name == "T":
+        return 3e-3
+    return 1e-3 + abs(coarse - fd) / abs(fd)
+
+
 @pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden finite differences not generated")
-@pytest.mark.parametrize("precision,tol,kernel", [(64, 1e-3, L.LBM_KERNEL_REFERENCE), (32, 1e-2, L.LBM_KERNEL_REFERENCE),
-                                                  (32, 1e-2, L.LBM_KERNEL_FUSED)])
-def test_inversion_gradient_matches_oracle_finite_differences(precision, tol, kernel):
+@pytest.mark.parametrize("precision,kernel", [(64, L.LBM_KERNEL_REFERENCE), (32, L.LBM_KERNEL_REFERENCE),
+                                              (32, L.LBM_KERNEL_FUSED)])
+def test_inversion_gradient_matches_oracle_finite_differences(precision, kernel):
+    """Each sampled derivative (15 wall angles next to the contact lines and T)
+    against the FP64 oracle's central difference, relative to its own size:
+    |adjoint - fd| <= tol |fd| + 2 err (err: the difference's noise estimate)."""
     meta, h_t, rows = _golden()
     ac = I.adjoint_case()
     nx, ny = ac["nx"], ac["ny"]
@@ -210,11 +236,10 @@ def test_inversion_gradient_matches_oracle_finite_differences(precision, tol, ke
         if precision == 64:
             assert loss == pytest.approx(meta["loss"], rel=1e-10)
         dth, dT, _ = L.lbm_adjoint_backward(s.ctx, g)
-    scale = max(abs(v) for _, _, v in rows)
-    for name, idx, fd in rows:
+    for name, idx, fd, err, coarse in rows:
         ad = dT if name == "T" else dth[0, idx]
-        ref = scale if name == "theta" else abs(fd)
-        assert abs(ad - fd) <= tol * max(abs(fd), 1e-3 * ref), (name, idx, ad, fd)
+        tol = _tol(precision, name, fd, coarse)
+        assert abs(ad - fd) <= tol * abs(fd) + 2.0 * err, (name, idx, ad, fd, err, tol)
 
 
 @pytest.mark.parametrize("precision", [64, 32])
