@@ -190,7 +190,9 @@ int lbm_create_with_buffer(int nx, int ny, const lbm_eos *eos, double T, double 
 
 /* f := f_eq(rho, u = 0) (Eq. 4 equilibria mapped back by M^-1) at every fluid
  * node, from nx*ny host densities (wall-row entries ignored).  Densities must
- * be finite and > 0 at fluid nodes (else LBM_EINVAL). */
+ * be finite and > 0 at fluid nodes (else LBM_EINVAL, and the state is left as
+ * it was).  Pinned (page-locked) host memory is read by the device in place;
+ * other host memory is first copied to the device.  Synchronises. */
 int lbm_set_rho(lbm_ctx *ctx, const double *rho);
 
 /* Initial droplets built on the device: rho = max over droplets k of
@@ -211,9 +213,10 @@ int lbm_step(lbm_ctx *ctx, int nsteps);
 /* Synchronise and read the device stability flag: LBM_OK or LBM_EUNSTABLE. */
 int lbm_status(lbm_ctx *ctx);
 
-/* Density at every node (nx*ny doubles): sum_a f_a (summed in double) at
- * fluid nodes, 0 on the solid rows.  The ghost densities that the wall rule
- * gives the solid rows for the current state come from lbm_get_fields. */
+/* Density at every node (nx*ny doubles): sum_a f_a (summed in double, left
+ * to right) at fluid nodes, 0 on the solid rows.  The ghost densities that the
+ * wall rule gives the solid rows for the current state come from
+ * lbm_get_fields.  Synchronises. */
 int lbm_get_rho(lbm_ctx *ctx, double *rho);
 
 /* Velocity u = (sum_a f_a e_a + F/2)/rho (the half-force shifted velocity of

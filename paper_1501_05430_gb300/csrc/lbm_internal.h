@@ -61,6 +61,8 @@ struct lbm_ctx {
   struct lbm_tape *tape; // adjoint record (lbm_adjoint.cu); NULL when none
   int *d_flag;           // [0]: instability, [1]: timeout, [2]: lbm_set_rho input check
   double *d_rho64;       // nx*ny, measurement density
+  cudaStream_t xfer;     // lbm_get_rho: copy stream and its chunk events (lazy; NULL until first needed)
+  cudaEvent_t xfer_ev[8];
   void *d_fields;        // 3*nx*ny reals: rho, psi, U (reference kernels)
   double *d_aux;         // 7*nx*ny doubles for lbm_get_u / lbm_get_fields (lazy)
   double *d_red;         // reduction partials
@@ -89,9 +91,10 @@ cudaError_t lbm_ref_collide(const lbm_ctx *C, const void *fin, void *fout, const
                             unsigned long long *launches);
 cudaError_t lbm_ref_macro(const lbm_ctx *C, const void *f, const void *fields, double *out7,
                           unsigned long long *launches);
-cudaError_t lbm_ref_set_rho(const lbm_ctx *C, const double *rho, void *f, unsigned long long *launches);
-// *bad |= 1 if a fluid-node density is not finite or not > 0 (bad zeroed by the caller)
-cudaError_t lbm_ref_check_rho(const lbm_ctx *C, const double *rho, int *bad, unsigned long long *launches);
+// f := f_eq(rho, 0) from device or mapped host densities; with bad != NULL,
+// *bad |= 1 if a fluid-node density is not finite or not > 0 (bad zeroed by
+// the caller; f is written all the same)
+cudaError_t lbm_ref_set_rho(const lbm_ctx *C, const double *rho, void *f, int *bad, unsigned long long *launches);
 cudaError_t lbm_ref_droplets(const lbm_ctx *C, int n, const double *drop, double width, double *rho,
                              unsigned long long *launches);
 
@@ -107,6 +110,9 @@ void lbm_adjoint_free_tape(lbm_ctx *C);
 
 // ---- lbm_measure.cu: reductions -------------------------------------------
 cudaError_t lbm_rho64(const lbm_ctx *C, const void *f, double *rho, unsigned long long *launches);
+// the same for rows [row0, row1) only (rho indexed like the whole field)
+cudaError_t lbm_rho64_rows(const lbm_ctx *C, const void *f, double *rho, int row0, int row1,
+                           unsigned long long *launches);
 cudaError_t lbm_reduce_mass(const lbm_ctx *C, const double *rho, double *partial, int npart, double *res,
                             unsigned long long *launches);
 cudaError_t lbm_reduce_max_speed(const lbm_ctx *C, const double *ux, const double *uy, double *partial,

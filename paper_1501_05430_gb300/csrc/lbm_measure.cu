@@ -12,16 +12,72 @@
 
 namespace {
 
+// The left-to-right double sum (((0 + f_0) + f_1) + ...) + f_8 of nine
+// floats, bit for bit, mostly without FP64 instructions (GB300 issues FP64 at
+// a small fraction of its FP32 rate).  When the nonzero terms span at most 26
+// binades (exponents emin..emin+25), each term is an integer multiple of
+// u = 2^(emin - 150) below 2^49 u, so every partial sum is a multiple of u
+// below 9 * 2^49 u < 2^53 u: exactly representable in double.  The double
+// additions are then exact, and the sum is the integer total S times u,
+// assembled directly as a double (exact cancellation gives +0, as the double
+// additions starting from +0 do).  Wider spans and subnormal, infinite or NaN
+// terms take the double additions.
+__device__ __forceinline__ double sum9(const float (&v)[9]) {
+  int emin = 255, emax = 0;
+  bool plain = true;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const unsigned u = __float_as_uint(v[a]);
+    const int e = (int)((u >> 23) & 255u);
+    plain &= e != 255 && (e != 0 || (u & 0x7fffffu) == 0u);
+    if (e != 0) {
+      emin = min(emin, e);
+      emax = max(emax, e);
+    }
+  }
+  if (plain && emax - emin <= 25) {
+    long long S = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const unsigned u = __float_as_uint(v[a]);
+      const int e = (int)((u >> 23) & 255u);
+      if (e != 0) {
+        const long long m = (long long)((u & 0x7fffffu) | 0x800000u) << (e - emin);
+        S += (u >> 31) ? -m : m;
+      }
+    }
+    if (S == 0) return 0.0;
+    const unsigned long long A = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+    const int p = 63 - __clzll((long long)A);  // p <= 52
+    const unsigned long long bits = ((unsigned long long)(S < 0) << 63) |
+                                    ((unsigned long long)(p + emin - 150 + 1023) << 52) |
+                                    ((A << (52 - p)) & 0xfffffffffffffull);
+    return __longlong_as_double((long long)bits);
+  }
+  double r = 0.0;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) r = r + (double)v[a];
+  return r;
+}
+
 // rho = sum_a f_a accumulated in double, left to right, at fluid nodes; 0 on
-// the solid rows.
+// the solid rows; nodes [i0, i1) of the field.
 template <typename R>
-__global__ void k_rho64(int nx, int ny, int walls, const R *__restrict__ f, double *__restrict__ rho) {
+__global__ void k_rho64(int nx, int ny, int walls, const R *__restrict__ f, double *__restrict__ rho, size_t i0,
+                        size_t i1) {
   size_t n = (size_t)nx * ny;
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  size_t i = i0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= i1) return;
   int y = (int)(i / nx);
   if (walls && (y == 0 || y == ny - 1)) {
     rho[i] = 0.0;
+    return;
+  }
+  if (sizeof(R) == sizeof(float)) {
+    float v[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = (float)f[a * n + i];
+    rho[i] = sum9(v);
     return;
   }
   double r = 0.0;
@@ -31,23 +87,27 @@ __global__ void k_rho64(int nx, int ny, int walls, const R *__restrict__ f, doub
 }
 
 // The same for FP32 states with nx % 4 == 0: four consecutive nodes of one
-// row per thread (16-byte loads of each plane, 2 x 16-byte stores), summed in
-// the same order as k_rho64.
-__global__ void k_rho64_x4(int nx, int ny, int walls, const float4 *__restrict__ f, double2 *__restrict__ rho) {
+// row per thread (16-byte loads of each plane, 2 x 16-byte stores); groups of
+// four [q0, q1).
+__global__ void k_rho64_x4(int nx, int ny, int walls, const float4 *__restrict__ f, double2 *__restrict__ rho,
+                           size_t q0, size_t q1) {
   const size_t n4 = (size_t)nx * ny / 4;
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n4) return;
+  const size_t i = q0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q1) return;
   const int y = (int)((4 * i) / nx);
   double2 lo = make_double2(0.0, 0.0), hi = lo;
   if (!(walls && (y == 0 || y == ny - 1))) {
+    float v0[9], v1[9], v2[9], v3[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const float4 v = f[a * n4 + i];
-      lo.x = lo.x + (double)v.x;
-      lo.y = lo.y + (double)v.y;
-      hi.x = hi.x + (double)v.z;
-      hi.y = hi.y + (double)v.w;
+      v0[a] = v.x;
+      v1[a] = v.y;
+      v2[a] = v.z;
+      v3[a] = v.w;
     }
+    lo = make_double2(sum9(v0), sum9(v1));
+    hi = make_double2(sum9(v2), sum9(v3));
   }
   rho[2 * i] = lo;
   rho[2 * i + 1] = hi;
@@ -231,16 +291,24 @@ inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t lbm_rho64(const lbm_ctx *C, const void *f, double *rho, unsigned long long *launches) {
-  size_t n = (size_t)C->nx * C->ny;
+cudaError_t lbm_rho64_rows(const lbm_ctx *C, const void *f, double *rho, int row0, int row1,
+                           unsigned long long *launches) {
+  const size_t i0 = (size_t)row0 * C->nx, i1 = (size_t)row1 * C->nx;
+  if (i1 <= i0) return cudaSuccess;
   if (C->precision == 64)
-    k_rho64<double><<<nblk(n, 256), 256, 0, C->stream>>>(C->nx, C->ny, C->walls, (const double *)f, rho);
+    k_rho64<double><<<nblk(i1 - i0, 256), 256, 0, C->stream>>>(C->nx, C->ny, C->walls, (const double *)f, rho, i0,
+                                                                i1);
   else if (C->nx % 4 == 0 && ((uintptr_t)f & 15) == 0 && ((uintptr_t)rho & 15) == 0)
-    k_rho64_x4<<<nblk(n / 4, 256), 256, 0, C->stream>>>(C->nx, C->ny, C->walls, (const float4 *)f, (double2 *)rho);
+    k_rho64_x4<<<nblk((i1 - i0) / 4, 256), 256, 0, C->stream>>>(C->nx, C->ny, C->walls, (const float4 *)f,
+                                                                 (double2 *)rho, i0 / 4, i1 / 4);
   else
-    k_rho64<float><<<nblk(n, 256), 256, 0, C->stream>>>(C->nx, C->ny, C->walls, (const float *)f, rho);
+    k_rho64<float><<<nblk(i1 - i0, 256), 256, 0, C->stream>>>(C->nx, C->ny, C->walls, (const float *)f, rho, i0, i1);
   ++*launches;
   return cudaGetLastError();
+}
+
+cudaError_t lbm_rho64(const lbm_ctx *C, const void *f, double *rho, unsigned long long *launches) {
+  return lbm_rho64_rows(C, f, rho, 0, C->ny, launches);
 }
 
 cudaError_t lbm_reduce_mass(const lbm_ctx *C, const double *rho, double *partial, int npart, double *res,

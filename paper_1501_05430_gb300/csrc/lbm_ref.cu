@@ -10,8 +10,7 @@
 // streaming of Eq. 1 with half-way bounce-back).  The fused FP32 kernel (lbm_fused.cu) computes the
 // same step in one pass; these kernels also serve the macroscopic getters.
 #include <math.h>
-
-#include <algorithm>
+#include <stdint.h>
 
 #include "lbm_internal.h"
 #include "lbm_ref_node.cuh"
@@ -140,12 +139,21 @@ __global__ void k_macro(lbm_dev_params P, const R *__restrict__ f, const R *__re
   out7[6 * n + i] = (double)Qxy;
 }
 
+// A density a state may start from: finite and > 0.  Tested on the bits
+// (0 < bits < the bits of +infinity), without FP64 instructions.
+__device__ __forceinline__ bool rho_ok(double r) {
+  const long long b = __double_as_longlong(r);
+  return b > 0 && b < 0x7ff0000000000000ll;
+}
+
 // f := M^-1 m_eq(rho, 0).  The double instantiation evaluates it in the
 // canonical order; the float one uses its closed form rho * (4/9, 1/9 x4,
 // 1/36 x4) in double and rounds once (the same values up to the last bit of
-// double, without nine double divisions per node).
+// double, without nine double divisions per node).  rho may be device memory
+// or mapped (pinned) host memory; with bad != NULL, *bad |= 1 for a fluid
+// density that fails rho_ok (the nodes are written all the same).
 template <typename R>
-__global__ void k_set_rho(lbm_dev_params P, const double *__restrict__ rho, R *__restrict__ f) {
+__global__ void k_set_rho(lbm_dev_params P, const double *__restrict__ rho, R *__restrict__ f, int *bad) {
   size_t n = (size_t)P.nx * P.ny;
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -155,6 +163,7 @@ __global__ void k_set_rho(lbm_dev_params P, const double *__restrict__ rho, R *_
     return;
   }
   double r = rho[i], vx = 0.0, vy = 0.0;
+  if (bad && !rho_ok(r)) atomicOr(bad, 1);
   if (sizeof(R) == sizeof(float)) {
     const double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w2 = 1.0 / 36.0;
     f[i] = (R)(r * w0);
@@ -178,6 +187,30 @@ __global__ void k_set_rho(lbm_dev_params P, const double *__restrict__ rho, R *_
       if (MC(k, a) != 0.0) acc = acc + MC(k, a) * q[k];
     f[a * n + i] = (R)acc;
   }
+}
+
+// The float closed form for nx % 4 == 0: four consecutive nodes of one row
+// per thread (two 16-byte loads of rho, one 16-byte store per plane).
+__global__ void k_set_rho_x4(int nx, int ny, int walls, const double2 *__restrict__ rho, float4 *__restrict__ f,
+                             int *bad) {
+  const size_t n4 = (size_t)nx * ny / 4;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  const int y = (int)((4 * i) / nx);
+  float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0;
+  if (!(walls && (y == 0 || y == ny - 1))) {
+    const double2 a = rho[2 * i], b = rho[2 * i + 1];
+    if (bad && !(rho_ok(a.x) && rho_ok(a.y) && rho_ok(b.x) && rho_ok(b.y))) atomicOr(bad, 1);
+    const double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w2 = 1.0 / 36.0;
+    q0 = make_float4((float)(a.x * w0), (float)(a.y * w0), (float)(b.x * w0), (float)(b.y * w0));
+    q1 = make_float4((float)(a.x * w1), (float)(a.y * w1), (float)(b.x * w1), (float)(b.y * w1));
+    q2 = make_float4((float)(a.x * w2), (float)(a.y * w2), (float)(b.x * w2), (float)(b.y * w2));
+  }
+  f[i] = q0;
+#pragma unroll
+  for (int k = 1; k < 5; ++k) f[k * n4 + i] = q1;
+#pragma unroll
+  for (int k = 5; k < 9; ++k) f[k * n4 + i] = q2;
 }
 
 // Droplet density field: max over droplets of the tanh profile.
@@ -242,34 +275,15 @@ cudaError_t lbm_ref_macro(const lbm_ctx *C, const void *f, const void *fields, d
 }
 
 // Input check of lbm_set_rho: every fluid-node density finite and > 0.
-static __global__ void k_check_rho(int nx, int ny, int walls, const double *__restrict__ rho, int *bad) {
-  const size_t n = (size_t)nx * ny;
-  const size_t lo = walls ? (size_t)nx : 0, hi = walls ? n - nx : n;
-  int b = 0;
-  for (size_t i = lo + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (size_t)gridDim.x * blockDim.x) {
-    const double r = rho[i];
-    b |= !(r > 0.0) || !isfinite(r);
-  }
-  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
-}
-
-cudaError_t lbm_ref_check_rho(const lbm_ctx *C, const double *rho, int *bad, unsigned long long *launches) {
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t n = (size_t)C->nx * C->ny;
-  const int blocks = (int)std::min<size_t>(nblk(n, 256), (size_t)std::max(1, nsm) * 8);
-  k_check_rho<<<blocks, 256, 0, C->stream>>>(C->nx, C->ny, C->walls, rho, bad);
-  ++*launches;
-  return cudaGetLastError();
-}
-
-cudaError_t lbm_ref_set_rho(const lbm_ctx *C, const double *rho, void *f, unsigned long long *launches) {
+cudaError_t lbm_ref_set_rho(const lbm_ctx *C, const double *rho, void *f, int *bad, unsigned long long *launches) {
   size_t n = (size_t)C->nx * C->ny;
   if (C->precision == 64)
-    k_set_rho<double><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, rho, (double *)f);
+    k_set_rho<double><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, rho, (double *)f, bad);
+  else if (C->nx % 4 == 0 && ((uintptr_t)rho & 15) == 0 && ((uintptr_t)f & 15) == 0)
+    k_set_rho_x4<<<nblk(n / 4, 256), 256, 0, C->stream>>>(C->nx, C->ny, C->walls, (const double2 *)rho,
+                                                          (float4 *)f, bad);
   else
-    k_set_rho<float><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, rho, (float *)f);
+    k_set_rho<float><<<nblk(n, 256), 256, 0, C->stream>>>(C->dp, rho, (float *)f, bad);
   ++*launches;
   return cudaGetLastError();
 }
