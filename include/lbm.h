@@ -364,9 +364,13 @@ typedef struct {
 
 /* Launch shape.  Zero fields take the defaults in brackets. */
 typedef struct {
-  int threads;           /* threads per CTA: 256 (the one shape) [256]; thread t < nx/2
-                            owns columns t and t + nx/2 of a row */
-  int ctas_per_sm;       /* cap on resident CTAs per SM [occupancy maximum] */
+  int threads;           /* 256 [default]: every instance in one launch of 256-thread
+                            CTAs; 128: the instances up to 256 wide in a launch of their
+                            own with 128-thread CTAs (a 256-wide row then keeps every
+                            thread busy), the wider ones in 256-thread CTAs.  Thread
+                            t < nx/2 owns columns t and t + nx/2 of a row */
+  int ctas_per_sm;       /* cap on resident CTAs per SM, in 256-thread CTAs (twice as
+                            many 128-thread ones) [occupancy maximum] */
   int stages;            /* shared memory of the copy ring, in rows of the widest
                             instance, 3..6 [4]; each work item repacks it into
                             min(16, stages x widest / nx) rows of its own width */
@@ -428,7 +432,10 @@ int lbm_batch_get_config(const lbm_batch *b, lbm_batch_config *cfg);
 /* Install a launch shape (validated as in lbm_batch_create). */
 int lbm_batch_set_config(lbm_batch *b, const lbm_batch_config *cfg);
 /* Plan of the current shape: CTAs per launch, work items, dynamic shared
- * memory per CTA, resident CTAs per SM.  Any pointer may be NULL. */
+ * memory per CTA, resident CTAs per SM.  With threads = 128 and instances on
+ * both sides of 256 columns, CTAs and items are summed over the two launches,
+ * the shared memory is the larger one and the CTAs per SM are the 256-thread
+ * launch's.  Any pointer may be NULL. */
 int lbm_batch_get_plan(const lbm_batch *b, int *grid, int *items, int *smem_bytes, int *ctas_per_sm);
 /* Kernel launches issued by lbm_batch_step so far (graph replays included). */
 unsigned long long lbm_batch_launch_count(const lbm_batch *b);

@@ -51,10 +51,14 @@ using lbm_node::eos_node;
 using lbm_node::eos_node2;
 using lbm_node::ghost_value;
 
-constexpr int kNT = 256;       // threads per CTA: thread t < nx/2 owns columns t and t + nx/2 (one lane pair)
-constexpr int kMaxNx = 2 * kNT;  // widest instance
+// Threads per CTA NT (a template parameter): thread t < nx/2 owns columns t
+// and t + nx/2 (one lane pair), so an instance is at most 2 NT wide.  The
+// default shape runs every instance in 256-thread CTAs; the split shape runs
+// the instances up to 256 wide in a launch of their own with 128-thread CTAs,
+// where a 256-wide row keeps every thread busy (in a 256-thread CTA half the
+// warps would wait at each row's barrier).
+constexpr int kMaxNx = 512;      // widest instance
 constexpr int kSlots = 4;        // window rows (ring)
-constexpr int kWP = kNT + 2;     // paired window entries e = -1 .. nx/2 at index e + 1
 constexpr int kMaxRing = 16;     // row slots (and mbarriers) of the copy ring at most
 
 // Per-instance block: the node-function fields (same names as the fused
@@ -154,7 +158,7 @@ __device__ bool wait_ge(const unsigned *p, unsigned target, const int *abort, un
 // Shared memory of a CTA (dynamic part, 128-byte aligned base).
 struct Smem {
   float *stage;              // S x 9 x nxs floats: rows loaded by bulk copies (K slots of 9 x nx per item)
-  float2 *wpsi, *wsq;        // [kSlots][kWP]: psi and psi^2 in lane pairs (entry e = columns e, e + nx/2)
+  float2 *wpsi, *wsq;        // [kSlots][NT + 2]: psi and psi^2 in lane pairs (entry e = columns e, e + nx/2)
   float *wrho;               // [nxs + 2]: boundary-row densities, column c at c + 1 (periodic copies at 0, nx + 1)
   unsigned long long *bars;  // [kMaxRing]: one mbarrier per row slot
 };
@@ -176,9 +180,10 @@ struct Ring {
 // of S stages; a stage is read when its row arrives (rho) and again when the
 // row is collided one iteration later, then refilled.
 // Returns false if a wait on a row ran out (the CTA then aborts).
-template <bool UNIT>
+template <bool UNIT, int NT>
 __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__ src, float *__restrict__ dst,
                       const Smem &M, int nxs, int S, Ring &rg, unsigned long long wait_ns, bool &bad) {
+  constexpr int kWP = NT + 2;  // paired window entries e = -1 .. nx/2 at index e + 1
   const int tid = threadIdx.x;
   const int nx = P.nx, ny = P.ny;
   const size_t n = (size_t)nx * ny;
@@ -390,7 +395,9 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
   return ok;
 }
 
-__global__ void __launch_bounds__(kNT, 3) k_batch(BatchArgs A) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) k_batch(BatchArgs A) {
+  constexpr int kWP = NT + 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ BInst sP;
   __shared__ BItem s_it;
@@ -455,8 +462,8 @@ __global__ void __launch_bounds__(kNT, 3) k_batch(BatchArgs A) {
     const int par = A.cur[it.inst] ^ ((A.phase + s_step) & 1);
     bool bad = false;
     if (!s_skip) {
-      bool ok = sP.unit ? sweep<true>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad)
-                        : sweep<false>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad);
+      bool ok = sP.unit ? sweep<true, NT>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad)
+                        : sweep<false, NT>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad);
       if (!ok) s_timeout = 1;
     }
     if (bad) s_bad = 1;
@@ -494,10 +501,10 @@ __global__ void __launch_bounds__(kNT, 3) k_batch(BatchArgs A) {
   }
 }
 
-const void *kernel_ptr() { return (const void *)k_batch; }
+const void *kernel_ptr(int nt) { return nt == 128 ? (const void *)k_batch<128> : (const void *)k_batch<256>; }
 
-size_t smem_bytes(int nxs, int stages) {
-  return 128 + (size_t)stages * 9 * nxs * sizeof(float) + (size_t)2 * kSlots * kWP * sizeof(float2) +
+size_t smem_bytes(int nxs, int stages, int nt) {
+  return 128 + (size_t)stages * 9 * nxs * sizeof(float) + (size_t)2 * kSlots * (nt + 2) * sizeof(float2) +
          (size_t)((nxs + 2 + 1) & ~1) * sizeof(float) + (size_t)kMaxRing * 8;
 }
 
@@ -517,20 +524,28 @@ struct lbm_batch {
   size_t pool_bytes;
   std::vector<size_t> offset; // byte offset of each instance's state in the pool
   std::vector<BInst> hinst;
-  std::vector<BItem> items;
+  // the launches of one chunk of steps: [0] 256-thread CTAs, [1] 128-thread
+  // CTAs (split shape: the instances up to 256 wide); a part without items is
+  // not launched
+  struct Part {
+    int nt;
+    std::vector<BItem> items;
+    BItem *d_items;
+    size_t d_items_cap;
+    int grid, nxs, smem, occ;
+  } part[2];
   std::vector<int> hcur;      // array index of each instance's state at phase 0
   int phase;                  // steps since hcur was uploaded, mod 2
   BInst *d_inst;
-  BItem *d_items;
   unsigned *d_bar;            // [n] arrival counters + [1] work counter
   int *d_abort;
   int *d_iflag;
   unsigned long long *d_work;  // [n] fluid-node updates computed per instance
   int *d_cur;
-  size_t d_items_cap;
-  int grid, nxs, smem, occ, nsm;
+  int nsm;
   cudaGraphExec_t graph[2];   // per starting phase
   int graph_steps;
+  unsigned long long graph_kernels;  // kernels one graph replay launches
   unsigned long long launches;
   long long steps;
   int status;
@@ -559,8 +574,8 @@ int resolve_config(const lbm_batch *B, const lbm_batch_config *in, lbm_batch_con
   lbm_batch_config c = *in;
   int nxmax = 0;
   for (int i = 0; i < B->n; ++i) nxmax = std::max(nxmax, B->ctx[i]->nx);
-  if (c.threads == 0) c.threads = kNT;
-  if (c.threads != kNT) return LBM_EINVAL;
+  if (c.threads == 0) c.threads = 256;
+  if (c.threads != 256 && c.threads != 128) return LBM_EINVAL;
   if (nxmax > kMaxNx) return LBM_EUNSUPPORTED;
   if (c.stages == 0) c.stages = 4;
   if (c.stages < 3 || c.stages > 6) return LBM_EINVAL;
@@ -581,87 +596,107 @@ int resolve_config(const lbm_batch *B, const lbm_batch_config *in, lbm_batch_con
 // Items, CTA ranges, launch shape for B->cfg; uploads the tables.
 int plan(lbm_batch *B) {
   const lbm_batch_config &c = B->cfg;
-  B->items.clear();
-  int nxmax = 0;
+  int nxmax[2] = {0, 0};
+  for (int s = 0; s < 2; ++s) {
+    B->part[s].nt = s == 0 ? 256 : 128;
+    B->part[s].items.clear();
+    B->part[s].grid = B->part[s].nxs = B->part[s].smem = B->part[s].occ = 0;
+  }
   for (int i = 0; i < B->n; ++i) {
     const lbm_ctx *C = B->ctx[i];
-    nxmax = std::max(nxmax, C->nx);
+    const int s = c.threads == 128 && C->nx <= 256 ? 1 : 0;
+    std::vector<BItem> &items = B->part[s].items;
+    nxmax[s] = std::max(nxmax[s], C->nx);
     const int band = c.band_rows[size_class(C->nx)];
-    B->hinst[i].first = (int)B->items.size();
+    B->hinst[i].first = (int)items.size();
     int cnt = 0;
     for (int y = 1; y < C->ny - 1; y += band) {
-      B->items.push_back(BItem{i, y, std::min(y + band, C->ny - 1), 0});
+      items.push_back(BItem{i, y, std::min(y + band, C->ny - 1), 0});
       ++cnt;
     }
     B->hinst[i].items = cnt;
   }
-  const int nitems = (int)B->items.size();
-  if ((long long)nitems * c.steps_per_launch >= (1LL << 31)) return LBM_EUNSUPPORTED;
-  B->nxs = (nxmax + 3) & ~3;
-  B->smem = (int)smem_bytes(B->nxs, c.stages);
-  const void *kern = kernel_ptr();
-  int dev = 0, occ = 0, optin = 0;
+  int dev = 0, optin = 0;
   BCK(cudaGetDevice(&dev));
-  // the attribute is per kernel, not per batch: allow the device maximum so
-  // that batches (and autotuner trials) with different rings coexist
   BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  cudaFuncAttributes fa;
-  BCK(cudaFuncGetAttributes(&fa, kern));
-  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= the opt-in limit
-  if (B->smem > dyn_max) return LBM_EUNSUPPORTED;
-  BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
   BCK(cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, dev));
-  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kNT, B->smem));
-  if (occ < 1) return LBM_EUNSUPPORTED;
-  if (c.ctas_per_sm > 0 && c.ctas_per_sm < occ) occ = c.ctas_per_sm;
-  B->occ = occ;
-  B->grid = std::min(B->nsm * occ, nitems);
-  if ((size_t)nitems > B->d_items_cap) {
-    cudaFree(B->d_items);
-    B->d_items = nullptr;
-    BCK(cudaMalloc(&B->d_items, (size_t)nitems * sizeof(BItem)));
-    B->d_items_cap = nitems;
+  for (int s = 0; s < 2; ++s) {
+    lbm_batch::Part &P = B->part[s];
+    const int nitems = (int)P.items.size();
+    if (nitems == 0) continue;
+    if ((long long)nitems * c.steps_per_launch >= (1LL << 31)) return LBM_EUNSUPPORTED;
+    P.nxs = (nxmax[s] + 3) & ~3;
+    P.smem = (int)smem_bytes(P.nxs, c.stages, P.nt);
+    const void *kern = kernel_ptr(P.nt);
+    // the attribute is per kernel, not per batch: allow the device maximum so
+    // that batches (and autotuner trials) with different rings coexist
+    cudaFuncAttributes fa;
+    BCK(cudaFuncGetAttributes(&fa, kern));
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= the opt-in limit
+    if (P.smem > dyn_max) return LBM_EUNSUPPORTED;
+    BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+    int occ = 0;
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, P.nt, P.smem));
+    if (occ < 1) return LBM_EUNSUPPORTED;
+    // ctas_per_sm counts 256-thread CTAs; a 128-thread part may hold twice as many
+    const int cap = c.ctas_per_sm * (256 / P.nt);
+    if (c.ctas_per_sm > 0 && cap < occ) occ = cap;
+    P.occ = occ;
+    P.grid = std::min(B->nsm * occ, nitems);
+    if ((size_t)nitems > P.d_items_cap) {
+      cudaFree(P.d_items);
+      P.d_items = nullptr;
+      P.d_items_cap = 0;
+      BCK(cudaMalloc(&P.d_items, (size_t)nitems * sizeof(BItem)));
+      P.d_items_cap = nitems;
+    }
+    BCK(cudaMemcpyAsync(P.d_items, P.items.data(), (size_t)nitems * sizeof(BItem), cudaMemcpyHostToDevice,
+                        B->stream));
   }
-  BCK(cudaMemcpyAsync(B->d_items, B->items.data(), (size_t)nitems * sizeof(BItem), cudaMemcpyHostToDevice,
-                      B->stream));
   BCK(cudaMemcpyAsync(B->d_inst, B->hinst.data(), (size_t)B->n * sizeof(BInst), cudaMemcpyHostToDevice, B->stream));
   BCK(cudaStreamSynchronize(B->stream));
   drop_graphs(B);
   return LBM_OK;
 }
 
-// One launch of `steps` steps starting at parity `phase` (no synchronisation).
+// The launches of `steps` steps starting at parity `phase`, one per part
+// with items, in order on the stream (no synchronisation).  The parts hold
+// different instances, so they need no ordering among themselves.
 int launch(lbm_batch *B, int steps, int phase) {
-  BatchArgs A;
-  A.inst = B->d_inst;
-  A.items = B->d_items;
-  A.nitems = (int)B->items.size();
-  A.bar = B->d_bar;
-  A.next = B->d_bar + B->n;
-  A.abort = B->d_abort;
-  A.iflag = B->d_iflag;
-  A.work = B->d_work;
-  A.cur = B->d_cur;
-  A.steps = steps;
-  A.phase = phase;
-  A.nxs = B->nxs;
-  A.stages = B->cfg.stages;
-  A.wait_ns = (unsigned long long)(B->cfg.wait_seconds * 1e9);
-  A.hold = B->cfg.hold_instance;
-  BCK(cudaMemsetAsync(B->d_bar, 0, (size_t)(B->n + 1) * sizeof(unsigned), B->stream));
-  cudaLaunchConfig_t lc = {};
-  lc.gridDim = dim3(B->grid);
-  lc.blockDim = dim3(kNT);
-  lc.dynamicSmemBytes = B->smem;
-  lc.stream = B->stream;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the barriers need it
-  at[0].val.cooperative = 1;
-  lc.attrs = at;
-  lc.numAttrs = steps > 1 ? 1 : 0;
-  cudaError_t e = cudaLaunchKernelEx(&lc, k_batch, A);
-  BCK(e);
-  ++B->launches;
+  for (int s = 0; s < 2; ++s) {
+    const lbm_batch::Part &P = B->part[s];
+    if (P.items.empty()) continue;
+    BatchArgs A;
+    A.inst = B->d_inst;
+    A.items = P.d_items;
+    A.nitems = (int)P.items.size();
+    A.bar = B->d_bar;
+    A.next = B->d_bar + B->n;
+    A.abort = B->d_abort;
+    A.iflag = B->d_iflag;
+    A.work = B->d_work;
+    A.cur = B->d_cur;
+    A.steps = steps;
+    A.phase = phase;
+    A.nxs = P.nxs;
+    A.stages = B->cfg.stages;
+    A.wait_ns = (unsigned long long)(B->cfg.wait_seconds * 1e9);
+    A.hold = B->cfg.hold_instance;
+    BCK(cudaMemsetAsync(B->d_bar, 0, (size_t)(B->n + 1) * sizeof(unsigned), B->stream));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(P.grid);
+    lc.blockDim = dim3(P.nt);
+    lc.dynamicSmemBytes = P.smem;
+    lc.stream = B->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the barriers need it
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = steps > 1 ? 1 : 0;
+    cudaError_t e = P.nt == 128 ? cudaLaunchKernelEx(&lc, k_batch<128>, A) : cudaLaunchKernelEx(&lc, k_batch<256>, A);
+    BCK(e);
+    ++B->launches;
+  }
   return LBM_OK;
 }
 
@@ -733,14 +768,16 @@ int run_steps(lbm_batch *B, int nsteps) {
       cudaGraph_t g = nullptr;
       BCK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
       int st = LBM_OK;
+      const unsigned long long l0 = B->launches;
       for (int l = 0; l < G && st == LBM_OK; ++l) st = launch(B, k, p ^ (l * k & 1));
       cudaError_t e = cudaStreamEndCapture(B->stream, &g);
+      B->graph_kernels = B->launches - l0;
+      B->launches = l0;  // counted when replayed
       if (st != LBM_OK || e != cudaSuccess) {
         cudaGetLastError();
         if (g) cudaGraphDestroy(g);
         return LBM_ECUDA;
       }
-      B->launches -= G;  // counted when replayed
       e = cudaGraphInstantiate(&B->graph[p], g, 0);
       cudaGraphDestroy(g);
       BCK(e);
@@ -748,7 +785,7 @@ int run_steps(lbm_batch *B, int nsteps) {
     }
     while (nsteps - done >= B->graph_steps) {
       BCK(cudaGraphLaunch(B->graph[p], B->stream));
-      B->launches += G;
+      B->launches += B->graph_kernels;
       done += B->graph_steps;
     }
   }
@@ -1050,10 +1087,11 @@ int lbm_batch_node_updates(lbm_batch *B, unsigned long long *updates) {
 
 int lbm_batch_get_plan(const lbm_batch *B, int *grid, int *items, int *smem_bytes, int *ctas_per_sm) {
   if (!B) return LBM_EINVAL;
-  if (grid) *grid = B->grid;
-  if (items) *items = (int)B->items.size();
-  if (smem_bytes) *smem_bytes = B->smem;
-  if (ctas_per_sm) *ctas_per_sm = B->occ;
+  const lbm_batch::Part &P0 = B->part[0], &P1 = B->part[1];
+  if (grid) *grid = P0.grid + P1.grid;
+  if (items) *items = (int)(P0.items.size() + P1.items.size());
+  if (smem_bytes) *smem_bytes = std::max(P0.smem, P1.smem);
+  if (ctas_per_sm) *ctas_per_sm = P0.items.empty() ? P1.occ : P0.occ;
   return LBM_OK;
 }
 
@@ -1066,7 +1104,7 @@ void lbm_batch_destroy(lbm_batch *B) {
     if (C) lbm_destroy(C);
   cudaFree(B->pool);
   cudaFree(B->d_inst);
-  cudaFree(B->d_items);
+  for (int s = 0; s < 2; ++s) cudaFree(B->part[s].d_items);
   cudaFree(B->d_bar);
   cudaFree(B->d_abort);
   cudaFree(B->d_iflag);

@@ -63,11 +63,13 @@ def _close(cases):
         c.orc.close()
 
 
-def test_every_instance_matches_the_oracle():
+@pytest.mark.parametrize("threads", [256, 128])
+def test_every_instance_matches_the_oracle(threads):
     """Mixed batch, several items per instance (cross-CTA barriers), an odd
-    number of steps per launch: every instance's f against the oracle."""
+    number of steps per launch: every instance's f against the oracle.  With
+    128 threads the instances up to 256 wide run in a launch of their own."""
     cases = _cases()
-    with _batch(cases, band_rows=[4, 4, 4, 4], steps_per_launch=5) as b:
+    with _batch(cases, band_rows=[4, 4, 4, 4], steps_per_launch=5, threads=threads) as b:
         assert b.plan()["items"] > len(cases)
         b.step(12)
         st, inst = b.status()
@@ -86,6 +88,9 @@ SHAPES = [
     dict(stages=5, band_rows=[2, 7, 3, 5], steps_per_launch=16, ctas_per_sm=1),
     dict(threads=256, steps_per_launch=4, stages=4),
     dict(steps_per_launch=2, graph_launches=3),
+    dict(threads=128),
+    dict(threads=128, stages=3, band_rows=[2, 7, 3, 5], steps_per_launch=5, graph_launches=2),
+    dict(threads=128, stages=5, band_rows=[1, 64, 4, 16], steps_per_launch=1, ctas_per_sm=1),
 ]
 
 
@@ -119,6 +124,17 @@ def test_graph_replays_are_counted_and_match_direct_launches():
         g.step(19)  # two graph replays (8 steps each) + 3 direct steps
         d.step(19)
         assert g.launches() == d.launches() == 10
+        for a, b_ in zip(g.instances, d.instances):
+            assert np.array_equal(a.f(), b_.f())
+    # split shape: the 128- and 100-wide instances in 128-thread CTAs, the
+    # 260-wide one in 256-thread CTAs: two kernels per launch of the batch
+    with _batch(cases, stream=stream, steps_per_launch=2, graph_launches=4, threads=128) as g, \
+            _batch(cases, stream=stream, steps_per_launch=2, threads=128) as d:
+        g.step(19)
+        d.step(19)
+        assert g.launches() == d.launches() == 20
+        plan = g.plan()
+        assert plan["items"] == sum(-(-(c.ny - 2) // 32) for c in cases)
         for a, b_ in zip(g.instances, d.instances):
             assert np.array_equal(a.f(), b_.f())
     _close(cases)
