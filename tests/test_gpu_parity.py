@@ -158,11 +158,16 @@ def test_fp32_fused_matches_fp32_reference_kernels():
     b.close()
 
 
-def test_fp32_fused_full_size_throughput_workload():
-    """The 4096 x 2048 benchmark workload in the benchmark's launch
-    configuration: every node against the oracle after 2 steps."""
-    w = I.throughput()
+@pytest.mark.parametrize("recipe", ["throughput_cs", "throughput"])
+def test_fp32_fused_full_size_throughput_workload(recipe):
+    """The two 4096 x 2048 benchmark workloads (Carnahan-Starling with MRT
+    rates: the general-rate kernel; Table 1 with all rates 1: the unit-rate
+    kernel) in the benchmark's launch configuration: every node against the
+    oracle after 2 steps."""
+    w = getattr(I, recipe)()
     p = droplet_pair(w, precision=32, kernel=FUSED)
+    assert p.gpu.info.kernel_in_use == L.LBM_KERNEL_FUSED
+    assert (w.tau == 1.0 and not w.rates) == (recipe == "throughput")  # unit rates only for Table 1
     before = p.gpu.launches()
     assert p.step(2) == 0
     assert p.gpu.launches() - before == 2
@@ -183,17 +188,19 @@ def test_zero_steps_change_nothing(kernel):
     p.close()
 
 
-def test_fp32_fused_at_the_32_bit_offset_limit():
+@pytest.mark.parametrize("recipe", ["throughput_cs", "throughput"])
+def test_fp32_fused_at_the_32_bit_offset_limit(recipe):
     """The largest grid the fused kernel takes (9 nx ny just below 2^31, where
-    its 32-bit element offsets end): 32768 x 7281, 17 GB of distributions.
-    The initial state and the wall angles repeat every 256 columns, so after 2
+    its 32-bit element offsets end): 32768 x 7281, 17 GB of distributions,
+    with each benchmark recipe (general-rate and unit-rate kernels).  The
+    initial state and the wall angles repeat every 256 columns, so after 2
     steps every 256-column window equals the oracle run on a 256-wide periodic
     domain (x translation symmetry holds at any size); three windows are
     compared node by node."""
     tile, reps, ny = 256, 128, 7281
     nx = tile * reps
     assert 9 * nx * ny < 2 ** 31 <= 9 * nx * (ny + 1)
-    w = I.throughput(nx=tile, ny=ny)
+    w = getattr(I, recipe)(nx=tile, ny=ny)
     c = Case(tile, ny, t_over_tc=w.t_over_tc, tau=w.tau, theta=w.theta, rates=w.rates, precision=32,
              eos=w.eos, A=w.A, kappa=w.kappa, kernel=FUSED)
     rho_tile = I.droplet_field(tile, ny, w.droplets, c.rho_v, c.rho_l, w.width)
