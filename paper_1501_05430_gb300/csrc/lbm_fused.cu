@@ -147,7 +147,7 @@ struct Seq {
   __device__ bool solid(const FusedArgs &P) const { return P.walls && (v == 0 || v == P.ny - 1); }
 };
 
-template <bool UNIT, int NC>
+template <bool UNIT, int NC, int MCW>
 __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
     k_fused(const __grid_constant__ CUtensorMap tm_main, const __grid_constant__ CUtensorMap tm_halo, FusedArgs P) {
   static_assert(NC == 2, "two columns per thread: one lane pair");
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
       qn[7] = qm[i - 1];
       pn[8] = pm[i + 1];
       qn[8] = qm[i + 1];
-      collide_node2<UNIT>(P, fcol, pn, qn, make_float2(r0w[c0 + 2], r0w[c1 + 2]), y, fs2);
+      collide_node2<UNIT, MCW>(P, fcol, pn, qn, make_float2(r0w[c0 + 2], r0w[c1 + 2]), y, fs2);
       if (!UNIT && !wall_dn && !wall_up && y >= 1 && y <= P.ny - 2 && x0 >= 1 && x0 + W <= P.nx - 1) {
         // a row away from the walls and the y wrap, in a strip away from the x wrap:
         // every destination is a fixed offset from the node, and column c1
@@ -515,7 +515,12 @@ size_t smem_bytes(int stages) {
          (size_t)NSLOT * C::WIN * sizeof(float) + (size_t)stages * 8 + 16;
 }
 
-const void *kernel_ptr(bool unit) { return unit ? (const void *)k_fused<true, kNC> : (const void *)k_fused<false, kNC>; }
+// the four specialisations: collision (unit or general rates) x wetting rule
+// (geometric or Martys-Chen) fixed at compile time
+const void *kernel_ptr(bool unit, bool mc) {
+  if (mc) return unit ? (const void *)k_fused<true, kNC, 1> : (const void *)k_fused<false, kNC, 1>;
+  return unit ? (const void *)k_fused<true, kNC, 0> : (const void *)k_fused<false, kNC, 0>;
+}
 
 }  // namespace
 
@@ -537,7 +542,7 @@ int lbm_fused_plan(lbm_ctx *C) {
   // the diag(0,1,...,1) relaxation of Sec. 3.1 takes the specialised collision
   const lbm_dev_params &D = C->dp;
   C->fused_unit = D.s[1] == 1.0 && D.s[2] == 1.0 && D.s[4] == 1.0 && D.s[7] == 1.0;
-  const void *kern = kernel_ptr(C->fused_unit);
+  const void *kern = kernel_ptr(C->fused_unit, D.wetting == LBM_WET_MARTYS_CHEN);
   int dev = 0, nsm = 0, occ = 0, optin = 0;
   cudaGetDevice(&dev);
   // the attribute is per kernel, not per context: allow the device maximum so
@@ -642,8 +647,13 @@ cudaError_t launch_fused(lbm_ctx *C, const CUtensorMap &tm, const CUtensorMap &t
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl;
-  cudaError_t e = C->fused_unit ? cudaLaunchKernelEx(&cfg, k_fused<true, kNC>, tm, th, P)
-                                : cudaLaunchKernelEx(&cfg, k_fused<false, kNC>, tm, th, P);
+  cudaError_t e;
+  if (C->dp.wetting == LBM_WET_MARTYS_CHEN)
+    e = C->fused_unit ? cudaLaunchKernelEx(&cfg, k_fused<true, kNC, 1>, tm, th, P)
+                      : cudaLaunchKernelEx(&cfg, k_fused<false, kNC, 1>, tm, th, P);
+  else
+    e = C->fused_unit ? cudaLaunchKernelEx(&cfg, k_fused<true, kNC, 0>, tm, th, P)
+                      : cudaLaunchKernelEx(&cfg, k_fused<false, kNC, 0>, tm, th, P);
   ++*launches;
   return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -160,8 +160,10 @@ __device__ __forceinline__ void eos_node2(const PT &P, float2 rho, float2 &psi, 
 // pairs of the populations and of the neighbour values (psi, psi^2) at
 // x+e_0..x+e_8; rho: the two densities; fs: f*.  UNIT: every non-conserved
 // rate equals 1 (the relaxation matrix diag(0,1,...,1) of Sec. 3.1), so
-// m* = m_eq + S/2 + C needs only rho and j from f.
-template <bool UNIT, class PT>
+// m* = m_eq + S/2 + C needs only rho and j from f.  MCW: the wetting rule
+// when the caller fixes it at compile time (0 geometric, 1 Martys-Chen), or
+// -1 to read it from P -- a fixed rule leaves no branch in the arithmetic.
+template <bool UNIT, int MCW = -1, class PT>
 __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, const float2 *psi, const float2 *psi2,
                                               float2 rho, int y, float2 *fs) {
   const float2 w1 = bc2(1.0f / 3.0f), w2 = bc2(1.0f / 12.0f);
@@ -178,7 +180,8 @@ __device__ __forceinline__ void collide_node2(const PT &P, const float2 *f, cons
   const float2 gd57 = sub2(g[5], g[7]), gd86 = sub2(g[8], g[6]);
   float2 Fx = fma2(w1, sub2(g[1], g[3]), mul2(w2, add2(gd57, gd86)));
   float2 Fy = fma2(w1, sub2(g[2], g[4]), mul2(w2, sub2(gd57, gd86)));
-  if (P.wetting == LBM_WET_MARTYS_CHEN && P.walls) {
+  const bool mc = MCW < 0 ? P.wetting == LBM_WET_MARTYS_CHEN : MCW == 1;
+  if (mc && P.walls) {
     // Eq. 14 for flat solid rows: sum_a w_a S e_a = (0, -1/2) below, (0, 1/2) above
     const float ssy = (y == 1 ? -0.5f : 0.0f) + (y == P.ny - 2 ? 0.5f : 0.0f);
     Fy = fma2(mul2(bc2(-P.Gw), p0), bc2(ssy), Fy);
