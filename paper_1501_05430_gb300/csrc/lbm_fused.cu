@@ -147,7 +147,7 @@ struct Seq {
   __device__ bool solid(const FusedArgs &P) const { return P.walls && (v == 0 || v == P.ny - 1); }
 };
 
-template <bool UNIT, int NC, int MCW>
+template <bool UNIT, int NC, int MCW, int KIND>
 __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
     k_fused(const __grid_constant__ CUtensorMap tm_main, const __grid_constant__ CUtensorMap tm_halo, FusedArgs P) {
   static_assert(NC == 2, "two columns per thread: one lane pair");
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
                                    add2(add2(fin[4], fin[5]), add2(fin[6], fin[7]))),
                               fin[8]);
         float2 ps, ps2;
-        eos_node2(P, r, ps, ps2);
+        eos_node2<KIND>(P, r, ps, ps2);
         rcur[c0 + 2] = r.x;
         put(pcur, qcur, c0, ps.x, ps2.x);
         bad |= !(r.x > 0.0f) || r.x > P.rho_max;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         float r = (((src[0] + src[HB]) + (src[2 * HB] + src[3 * HB])) +
                    ((src[4 * HB] + src[5 * HB]) + (src[6 * HB] + src[7 * HB]))) +
                   src[8 * HB];
-        const float4 e = eos_node(P, r);
+        const float4 e = eos_node<KIND>(P, r);
         rcur[hc + 2] = r;
         put(pcur, qcur, hc, e.y, e.z);
       }
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         for (int j = 0; j < NC; ++j) {
           const int c = tid + j * NCONS;
           if (c < wr) {
-            const float4 e = ghost_node(P, r1w, rcur, c, x0 + c, 0);
+            const float4 e = ghost_node<KIND>(P, r1w, rcur, c, x0 + c, 0);
             gr[c + 2] = e.x;
             put(gp, gq, c, e.y, e.z);
           }
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         if (hact2) {
           int gx = x0 + hc;
           gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-          const float4 e = ghost_node(P, r1w, rcur, hc, gx, 0);
+          const float4 e = ghost_node<KIND>(P, r1w, rcur, hc, gx, 0);
           gr[hc + 2] = e.x;
           put(gp, gq, hc, e.y, e.z);
         }
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
             rcur[c + 2] = 0.0f;
             put(pcur, qcur, c, 0.0f, 0.0f);
           } else if (top) {
-            const float4 e = ghost_node(P, r1w, r2w, c, x0 + c, 1);
+            const float4 e = ghost_node<KIND>(P, r1w, r2w, c, x0 + c, 1);
             rcur[c + 2] = e.x;
             put(pcur, qcur, c, e.y, e.z);
           }
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
         } else if (top) {
           int gx = x0 + hc;
           gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-          const float4 e = ghost_node(P, r1w, r2w, hc, gx, 1);
+          const float4 e = ghost_node<KIND>(P, r1w, r2w, hc, gx, 1);
           rcur[hc + 2] = e.x;
           put(pcur, qcur, hc, e.y, e.z);
         }
@@ -515,11 +515,18 @@ size_t smem_bytes(int stages) {
          (size_t)NSLOT * C::WIN * sizeof(float) + (size_t)stages * 8 + 16;
 }
 
-// the four specialisations: collision (unit or general rates) x wetting rule
-// (geometric or Martys-Chen) fixed at compile time
-const void *kernel_ptr(bool unit, bool mc) {
-  if (mc) return unit ? (const void *)k_fused<true, kNC, 1> : (const void *)k_fused<false, kNC, 1>;
-  return unit ? (const void *)k_fused<true, kNC, 0> : (const void *)k_fused<false, kNC, 0>;
+// the eight specialisations: collision (unit or general rates) x wetting
+// rule (geometric or Martys-Chen) x EOS (Carnahan-Starling or Eq. 11), each
+// fixed at compile time so that no branch is left in the per-node arithmetic
+typedef void (*FusedKernel)(CUtensorMap, CUtensorMap, FusedArgs);
+template <bool UNIT, int MCW>
+FusedKernel pick_kind(int kind) {
+  return kind == LBM_EOS_CARNAHAN_STARLING ? (FusedKernel)k_fused<UNIT, kNC, MCW, LBM_EOS_CARNAHAN_STARLING>
+                                           : (FusedKernel)k_fused<UNIT, kNC, MCW, LBM_EOS_PIECEWISE>;
+}
+FusedKernel kernel_ptr(bool unit, bool mc, int kind) {
+  if (mc) return unit ? pick_kind<true, 1>(kind) : pick_kind<false, 1>(kind);
+  return unit ? pick_kind<true, 0>(kind) : pick_kind<false, 0>(kind);
 }
 
 }  // namespace
@@ -542,7 +549,7 @@ int lbm_fused_plan(lbm_ctx *C) {
   // the diag(0,1,...,1) relaxation of Sec. 3.1 takes the specialised collision
   const lbm_dev_params &D = C->dp;
   C->fused_unit = D.s[1] == 1.0 && D.s[2] == 1.0 && D.s[4] == 1.0 && D.s[7] == 1.0;
-  const void *kern = kernel_ptr(C->fused_unit, D.wetting == LBM_WET_MARTYS_CHEN);
+  const void *kern = (const void *)kernel_ptr(C->fused_unit, D.wetting == LBM_WET_MARTYS_CHEN, D.eos_kind);
   int dev = 0, nsm = 0, occ = 0, optin = 0;
   cudaGetDevice(&dev);
   // the attribute is per kernel, not per context: allow the device maximum so
@@ -647,13 +654,8 @@ cudaError_t launch_fused(lbm_ctx *C, const CUtensorMap &tm, const CUtensorMap &t
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl;
-  cudaError_t e;
-  if (C->dp.wetting == LBM_WET_MARTYS_CHEN)
-    e = C->fused_unit ? cudaLaunchKernelEx(&cfg, k_fused<true, kNC, 1>, tm, th, P)
-                      : cudaLaunchKernelEx(&cfg, k_fused<false, kNC, 1>, tm, th, P);
-  else
-    e = C->fused_unit ? cudaLaunchKernelEx(&cfg, k_fused<true, kNC, 0>, tm, th, P)
-                      : cudaLaunchKernelEx(&cfg, k_fused<false, kNC, 0>, tm, th, P);
+  const FusedKernel kern = kernel_ptr(C->fused_unit, C->dp.wetting == LBM_WET_MARTYS_CHEN, C->dp.eos_kind);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, tm, th, P);
   ++*launches;
   return e != cudaSuccess ? e : cudaGetLastError();
 }

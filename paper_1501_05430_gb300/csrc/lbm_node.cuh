@@ -64,10 +64,12 @@ __device__ __forceinline__ float sqrt0(float x) { return x * rsqrtf(fmaxf(x, 1.1
 //   -2U = rho (2/3 - 2 R T q + 2 a rho), q = (1 + e + e^2 - e^3)/(1 - e)^3,
 // or Eq. 11 written branch-free:
 //   p = rho th_v + (th_m - th_v)(rho - rho1)^+ + (th_l - th_m)(rho - rho2)^+.
-// The same operations, lane by lane, as eos_node2 (identical bits).
-template <class PT>
+// The same operations, lane by lane, as eos_node2 (identical bits).  KIND:
+// the EOS when the caller fixes it at compile time (LBM_EOS_*), or -1 to
+// read it from P.
+template <int KIND = -1, class PT>
 __device__ __forceinline__ float minus2u(const PT &P, float rho) {
-  if (P.kind == LBM_EOS_CARNAHAN_STARLING) {
+  if (KIND < 0 ? P.kind == LBM_EOS_CARNAHAN_STARLING : KIND == LBM_EOS_CARNAHAN_STARLING) {
     const float e = P.b4 * rho;
     const float om = fmaf(e, -1.0f, 1.0f);
     const float num = fmaf(e, fmaf(e, om, 1.0f), 1.0f);
@@ -79,16 +81,16 @@ __device__ __forceinline__ float minus2u(const PT &P, float rho) {
 
 // Window entry of one node: rho, psi and psi^2 = -2U (psi = 0 where U >= 0).
 // U itself is recovered as -psi^2/2 wherever the force needs it.
-template <class PT>
+template <int KIND = -1, class PT>
 __device__ __forceinline__ float4 eos_node(const PT &P, float rho) {
-  const float psi2 = fmaxf(0.0f, minus2u(P, rho));
+  const float psi2 = fmaxf(0.0f, minus2u<KIND>(P, rho));
   return make_float4(rho, sqrt0(psi2), psi2, 0.0f);
 }
 
 // Eqs. 19-21 ghost entry at column x from the boundary-row densities rl, ri1,
 // rr (at x-1, x, x+1) and the second-row density ri2 (at x); gx indexes the
 // wall coefficients; top: 0 or 1.
-template <class PT>
+template <int KIND = -1, class PT>
 __device__ __forceinline__ float4 ghost_value(const PT &P, float rl, float ri1, float rr, float ri2, int gx, int top) {
   float cc = (float)P.coef[top * P.nx + gx], cot = (float)P.coef[(2 + top) * P.nx + gx];
   float aa = rr - rl, g;
@@ -103,15 +105,15 @@ __device__ __forceinline__ float4 ghost_value(const PT &P, float rl, float ri1, 
     }
   }
   g = fminf(fmaxf(g, 0.0f), P.ghost_max);
-  return g < P.rho_max ? eos_node(P, g) : make_float4(g, 0.0f, 0.0f, 0.0f);  // psi = U = 0 at rho_max
+  return g < P.rho_max ? eos_node<KIND>(P, g) : make_float4(g, 0.0f, 0.0f, 0.0f);  // psi = U = 0 at rho_max
 }
 
 // The same from window rows: r1 boundary row, r2 second row, column c stored
 // at index c + 2.
-template <class PT>
+template <int KIND = -1, class PT>
 __device__ __forceinline__ float4 ghost_node(const PT &P, const float *r1, const float *r2, int c, int gx,
                                              int top) {
-  return ghost_value(P, r1[c + 1], r1[c + 2], r1[c + 3], r2[c + 2], gx, top);
+  return ghost_value<KIND>(P, r1[c + 1], r1[c + 2], r1[c + 3], r2[c + 2], gx, top);
 }
 
 // ---- two nodes at once ------------------------------------------------------
@@ -135,11 +137,11 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 
 // eos_node for two densities: the EOS arithmetic with packed instructions
 // (the reciprocal, the maxima and the square roots lane by lane); each lane
-// gets exactly eos_node's bits.
-template <class PT>
+// gets exactly eos_node's bits.  KIND as for minus2u.
+template <int KIND = -1, class PT>
 __device__ __forceinline__ void eos_node2(const PT &P, float2 rho, float2 &psi, float2 &psi2) {
   float2 m2u;
-  if (P.kind == LBM_EOS_CARNAHAN_STARLING) {
+  if (KIND < 0 ? P.kind == LBM_EOS_CARNAHAN_STARLING : KIND == LBM_EOS_CARNAHAN_STARLING) {
     const float2 e = mul2(bc2(P.b4), rho);
     const float2 om = fma2(e, bc2(-1.0f), bc2(1.0f));
     const float2 num = fma2(e, fma2(e, om, bc2(1.0f)), bc2(1.0f));
