@@ -180,7 +180,7 @@ struct Ring {
 // of S stages; a stage is read when its row arrives (rho) and again when the
 // row is collided one iteration later, then refilled.
 // Returns false if a wait on a row ran out (the CTA then aborts).
-template <bool UNIT, int NT>
+template <bool UNIT, int NT, int KIND, int MCW>
 __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__ src, float *__restrict__ dst,
                       const Smem &M, int nxs, int S, Ring &rg, unsigned long long wait_ns, bool &bad) {
   constexpr int kWP = NT + 2;  // paired window entries e = -1 .. nx/2 at index e + 1
@@ -188,7 +188,7 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
   const int nx = P.nx, ny = P.ny;
   const size_t n = (size_t)nx * ny;
   const int R = it.y1 - it.y0 + 2;
-  const bool geo = P.wetting == LBM_WET_GEOMETRIC;
+  const bool geo = MCW < 0 ? P.wetting == LBM_WET_GEOMETRIC : MCW == 0;
   const unsigned row_bytes = (unsigned)nx * 4u;
   const int K = min(kMaxRing, S * nxs / nx);  // row slots of 9 x nx floats (plane stride nx)
   rg.issued = rg.consumed = 0u;
@@ -275,7 +275,7 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
                               fin[8]);
         rc = r;
         float2 ps, ps2;
-        eos_node2(P, r, ps, ps2);
+        eos_node2<KIND>(P, r, ps, ps2);
         put(pcur, qcur, c0, ps.x, ps2.x);
         if (brow) putr(c0, r.x);
         bad |= !(r.x > 0.0f) || r.x > P.rho_max;
@@ -290,11 +290,11 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
       if (geo && it.y0 == 1 && v == 2) {
         float2 *gp = M.wpsi + (size_t)((j - 2) & 3) * kWP, *gq = M.wsq + (size_t)((j - 2) & 3) * kWP;
         if (act0) {
-          const float4 e = ghost_value(P, M.wrho[c0], M.wrho[c0 + 1], M.wrho[c0 + 2], rc.x, c0, 0);
+          const float4 e = ghost_value<KIND>(P, M.wrho[c0], M.wrho[c0 + 1], M.wrho[c0 + 2], rc.x, c0, 0);
           put(gp, gq, c0, e.y, e.z);
         }
         if (act1) {
-          const float4 e = ghost_value(P, M.wrho[c1], M.wrho[c1 + 1], M.wrho[c1 + 2], rc.y, c1, 0);
+          const float4 e = ghost_value<KIND>(P, M.wrho[c1], M.wrho[c1 + 1], M.wrho[c1 + 2], rc.y, c1, 0);
           put(gp, gq, c1, e.y, e.z);
         }
       }
@@ -303,12 +303,12 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
       // row from rows ny-2 (wrho) and ny-3 (registers); the bottom one is filled at v == 2.
       if (act0) {
         float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (geo) e = ghost_value(P, M.wrho[c0], M.wrho[c0 + 1], M.wrho[c0 + 2], rp2.x, c0, 1);
+        if (geo) e = ghost_value<KIND>(P, M.wrho[c0], M.wrho[c0 + 1], M.wrho[c0 + 2], rp2.x, c0, 1);
         put(pcur, qcur, c0, e.y, e.z);
       }
       if (act1) {
         float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (geo) e = ghost_value(P, M.wrho[c1], M.wrho[c1 + 1], M.wrho[c1 + 2], rp2.y, c1, 1);
+        if (geo) e = ghost_value<KIND>(P, M.wrho[c1], M.wrho[c1 + 1], M.wrho[c1 + 2], rp2.y, c1, 1);
         put(pcur, qcur, c1, e.y, e.z);
       }
     }
@@ -383,7 +383,7 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
       float2 fcol[9];
 #pragma unroll
       for (int a = 0; a < 9; ++a) fcol[a] = make_float2(fa[a * nx], fb[a * nx]);
-      collide_node2<UNIT>(P, fcol, pn, qn, rp, y, fs);
+      collide_node2<UNIT, MCW>(P, fcol, pn, qn, rp, y, fs);
       push((unsigned)c0, fs[0].x, fs[1].x, fs[2].x, fs[3].x, fs[4].x, fs[5].x, fs[6].x, fs[7].x, fs[8].x);
       if (act1) push((unsigned)c1, fs[0].y, fs[1].y, fs[2].y, fs[3].y, fs[4].y, fs[5].y, fs[6].y, fs[7].y, fs[8].y);
     }
@@ -395,7 +395,10 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
   return ok;
 }
 
-template <int NT>
+// KIND, MCW: the EOS and wetting rule of every instance of the launch when
+// they all share them (fixed at compile time: no branch in the per-node
+// arithmetic), else -1 (read per instance)
+template <int NT, int KIND, int MCW>
 __global__ void __launch_bounds__(NT, 768 / NT) k_batch(BatchArgs A) {
   constexpr int kWP = NT + 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -462,8 +465,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_batch(BatchArgs A) {
     const int par = A.cur[it.inst] ^ ((A.phase + s_step) & 1);
     bool bad = false;
     if (!s_skip) {
-      bool ok = sP.unit ? sweep<true, NT>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad)
-                        : sweep<false, NT>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad);
+      bool ok = sP.unit
+                    ? sweep<true, NT, KIND, MCW>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad)
+                    : sweep<false, NT, KIND, MCW>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad);
       if (!ok) s_timeout = 1;
     }
     if (bad) s_bad = 1;
@@ -501,7 +505,16 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_batch(BatchArgs A) {
   }
 }
 
-const void *kernel_ptr(int nt) { return nt == 128 ? (const void *)k_batch<128> : (const void *)k_batch<256>; }
+typedef void (*BatchKernel)(BatchArgs);
+template <int NT>
+BatchKernel pick_batch(int kind) {
+  if (kind == LBM_EOS_CARNAHAN_STARLING) return k_batch<NT, LBM_EOS_CARNAHAN_STARLING, 0>;
+  if (kind == LBM_EOS_PIECEWISE) return k_batch<NT, LBM_EOS_PIECEWISE, 0>;
+  return k_batch<NT, -1, -1>;
+}
+// kind: the EOS every instance of the launch shares, all with geometric
+// wetting; -1 otherwise (the generic kernel)
+BatchKernel kernel_ptr(int nt, int kind) { return nt == 128 ? pick_batch<128>(kind) : pick_batch<256>(kind); }
 
 size_t smem_bytes(int nxs, int stages, int nt) {
   return 128 + (size_t)stages * 9 * nxs * sizeof(float) + (size_t)2 * kSlots * (nt + 2) * sizeof(float2) +
@@ -529,6 +542,7 @@ struct lbm_batch {
   // not launched
   struct Part {
     int nt;
+    int kind;  // EOS kind shared by its instances, all geometric; -1: the generic kernel
     std::vector<BItem> items;
     BItem *d_items;
     size_t d_items_cap;
@@ -597,6 +611,7 @@ int resolve_config(const lbm_batch *B, const lbm_batch_config *in, lbm_batch_con
 int plan(lbm_batch *B) {
   const lbm_batch_config &c = B->cfg;
   int nxmax[2] = {0, 0};
+  int kind[2] = {-2, -2};  // -2: no instance yet
   for (int s = 0; s < 2; ++s) {
     B->part[s].nt = s == 0 ? 256 : 128;
     B->part[s].items.clear();
@@ -607,6 +622,8 @@ int plan(lbm_batch *B) {
     const int s = c.threads == 128 && C->nx <= 256 ? 1 : 0;
     std::vector<BItem> &items = B->part[s].items;
     nxmax[s] = std::max(nxmax[s], C->nx);
+    const int k = C->dp.wetting == LBM_WET_GEOMETRIC ? C->dp.eos_kind : -1;
+    kind[s] = kind[s] == -2 || kind[s] == k ? k : -1;
     const int band = c.band_rows[size_class(C->nx)];
     B->hinst[i].first = (int)items.size();
     int cnt = 0;
@@ -627,7 +644,8 @@ int plan(lbm_batch *B) {
     if ((long long)nitems * c.steps_per_launch >= (1LL << 31)) return LBM_EUNSUPPORTED;
     P.nxs = (nxmax[s] + 3) & ~3;
     P.smem = (int)smem_bytes(P.nxs, c.stages, P.nt);
-    const void *kern = kernel_ptr(P.nt);
+    P.kind = kind[s];
+    const void *kern = (const void *)kernel_ptr(P.nt, P.kind);
     // the attribute is per kernel, not per batch: allow the device maximum so
     // that batches (and autotuner trials) with different rings coexist
     cudaFuncAttributes fa;
@@ -693,7 +711,7 @@ int launch(lbm_batch *B, int steps, int phase) {
     at[0].val.cooperative = 1;
     lc.attrs = at;
     lc.numAttrs = steps > 1 ? 1 : 0;
-    cudaError_t e = P.nt == 128 ? cudaLaunchKernelEx(&lc, k_batch<128>, A) : cudaLaunchKernelEx(&lc, k_batch<256>, A);
+    cudaError_t e = cudaLaunchKernelEx(&lc, kernel_ptr(P.nt, P.kind), A);
     BCK(e);
     ++B->launches;
   }
