@@ -299,13 +299,30 @@ __global__ void __launch_bounds__(NCONS, Cfg<NC>::MIN_CTAS)
                               fin[8]);
         float2 ps, ps2;
         eos_node2<KIND>(P, r, ps, ps2);
-        rcur[c0 + 2] = r.x;
-        put(pcur, qcur, c0, ps.x, ps2.x);
-        bad |= !(r.x > 0.0f) || r.x > P.rho_max;
+        // unstable unless 0 < rho <= rho_max, tested on the bits: positive
+        // floats order like their bit patterns, and -0, negatives, +inf and
+        // NaN all land at or above rho_max's pattern after the decrement
+        const unsigned mx = __float_as_uint(P.rho_max);
         if (act1) {
+          // both columns: window entry c0 + 2 is the pair (c0, c1), one
+          // 64-bit store per quantity; the periodic copies as in put()
+          pcur[c0 + 2] = ps;
+          qcur[c0 + 2] = ps2;
+          if (c0 >= NCONS - 2) {
+            pcur[c0 - NCONS + 2].y = ps.x;
+            qcur[c0 - NCONS + 2].y = ps2.x;
+          }
+          if (c1 <= NCONS + 1) {
+            pcur[c1 + 2].x = ps.y;
+            qcur[c1 + 2].x = ps2.y;
+          }
+          rcur[c0 + 2] = r.x;
           rcur[c1 + 2] = r.y;
-          put(pcur, qcur, c1, ps.y, ps2.y);
-          bad |= !(r.y > 0.0f) || r.y > P.rho_max;
+          bad |= (__float_as_uint(r.x) - 1u >= mx) | (__float_as_uint(r.y) - 1u >= mx);
+        } else {
+          rcur[c0 + 2] = r.x;
+          put(pcur, qcur, c0, ps.x, ps2.x);
+          bad |= __float_as_uint(r.x) - 1u >= mx;
         }
       }
       if (hact) {
