@@ -276,14 +276,26 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
         rc = r;
         float2 ps, ps2;
         eos_node2<KIND>(P, r, ps, ps2);
-        put(pcur, qcur, c0, ps.x, ps2.x);
-        if (brow) putr(c0, r.x);
-        bad |= !(r.x > 0.0f) || r.x > P.rho_max;
-        if (act1) {
-          put(pcur, qcur, c1, ps.y, ps2.y);
-          if (brow) putr(c1, r.y);
-          bad |= !(r.y > 0.0f) || r.y > P.rho_max;
+        // window entry c0 + 1 is the pair (c0, c1): one 64-bit store per
+        // quantity; the pair reversed also fills entry 0 (columns nx-1 and
+        // h-1, from the thread with c0 = h-1) and entry h+1 (columns h and 0,
+        // from the thread with c0 = 0), as put() would
+        pcur[c0 + 1] = ps;
+        qcur[c0 + 1] = ps2;
+        if (c0 == h - 1 || c0 == 0) {
+          const int e = c0 == 0 ? h + 1 : 0;
+          pcur[e] = make_float2(ps.y, ps.x);
+          qcur[e] = make_float2(ps2.y, ps2.x);
         }
+        if (brow) {
+          putr(c0, r.x);
+          putr(c1, r.y);
+        }
+        // unstable unless 0 < rho <= rho_max, tested on the bits (positive
+        // floats order like their bit patterns; -0, negatives, +inf and NaN
+        // land at or above rho_max's pattern after the decrement)
+        const unsigned mx = __float_as_uint(P.rho_max);
+        bad |= (__float_as_uint(r.x) - 1u >= mx) | (__float_as_uint(r.y) - 1u >= mx);
       }
       // bottom ghost row (Eqs. 19-21) once rows 1 and 2 are in: row 1's
       // densities in wrho (written last iteration), row 2's in registers
