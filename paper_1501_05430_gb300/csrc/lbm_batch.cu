@@ -172,6 +172,7 @@ struct Ring {
   unsigned issued, consumed;  // loads of the current item
   unsigned wph;
   int K;
+  int islot, cslot;           // slots of the next load and of the next row to consume (issued, consumed mod K)
 };
 
 // One item of one step: stream virtual rows y0-1 .. y1 (halo and solid rows
@@ -192,6 +193,7 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
   const unsigned row_bytes = (unsigned)nx * 4u;
   const int K = min(kMaxRing, S * nxs / nx);  // row slots of 9 x nx floats (plane stride nx)
   rg.issued = rg.consumed = 0u;
+  rg.islot = rg.cslot = 0;
   rg.K = K;
   const int h = nx >> 1;  // lane-pair offset (nx is a multiple of 4)
   const int c0 = tid, c1 = tid + h;
@@ -209,7 +211,8 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
       const int v = it.y0 - 1 + jn;
       ++jn;
       if (v <= 0 || v >= ny - 1) continue;  // solid rows are not loaded
-      const int s = (int)(rg.issued % (unsigned)K);
+      const int s = rg.islot;
+      if (++rg.islot == K) rg.islot = 0;
       const unsigned bar = smem_u32(&M.bars[s]);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(9u * row_bytes)
                    : "memory");
@@ -257,7 +260,8 @@ __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__
     float2 *pcur = M.wpsi + (size_t)(j & 3) * kWP, *qcur = M.wsq + (size_t)(j & 3) * kWP;
     const bool solid = v == 0 || v == ny - 1;
     if (!solid) {
-      const int s = (int)(rg.consumed % (unsigned)K);
+      const int s = rg.cslot;
+      if (++rg.cslot == K) rg.cslot = 0;
       slot = s;
       const unsigned ph = (rg.wph >> s) & 1u;
       if (!mbar_wait(smem_u32(&M.bars[s]), ph, wait_ns)) ok = false;
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_batch(BatchArgs A) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  Ring rg{0u, 0u, 0u, 1};
+  Ring rg{0u, 0u, 0u, 1, 0, 0};
 
   for (;;) {
     if (tid == 0) {
