@@ -181,12 +181,14 @@ struct Ring {
 // of S stages; a stage is read when its row arrives (rho) and again when the
 // row is collided one iteration later, then refilled.
 // Returns false if a wait on a row ran out (the CTA then aborts).
-template <bool UNIT, int NT, int KIND, int MCW>
+// NX: the instance width when fixed at compile time (0: read from P), so that
+// every plane and lane-pair offset is an immediate.
+template <bool UNIT, int NT, int KIND, int MCW, int NX = 0>
 __device__ bool sweep(const BInst &P, const BItem &it, const float *__restrict__ src, float *__restrict__ dst,
                       const Smem &M, int nxs, int S, Ring &rg, unsigned long long wait_ns, bool &bad) {
   constexpr int kWP = NT + 2;  // paired window entries e = -1 .. nx/2 at index e + 1
   const int tid = threadIdx.x;
-  const int nx = P.nx, ny = P.ny;
+  const int nx = NX > 0 ? NX : P.nx, ny = P.ny;
   const size_t n = (size_t)nx * ny;
   const int R = it.y1 - it.y0 + 2;
   const bool geo = MCW < 0 ? P.wetting == LBM_WET_GEOMETRIC : MCW == 0;
@@ -481,9 +483,15 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_batch(BatchArgs A) {
     const int par = A.cur[it.inst] ^ ((A.phase + s_step) & 1);
     bool bad = false;
     if (!s_skip) {
-      bool ok = sP.unit
-                    ? sweep<true, NT, KIND, MCW>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad)
-                    : sweep<false, NT, KIND, MCW>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad);
+      bool ok;
+      if (sP.unit)
+        ok = sweep<true, NT, KIND, MCW>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad);
+      else if (NT == 256 && KIND >= 0 && sP.nx == 2 * NT)
+        // the widest instances, fixed at compile time in the specialised
+        // kernels (every thread owns one lane pair)
+        ok = sweep<false, NT, KIND, MCW, 2 * NT>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad);
+      else
+        ok = sweep<false, NT, KIND, MCW>(sP, it, sP.f[par], sP.f[par ^ 1], M, nxs, S, rg, A.wait_ns, bad);
       if (!ok) s_timeout = 1;
     }
     if (bad) s_bad = 1;
