@@ -489,7 +489,7 @@ def run_batched(args, stream):
         th, stg, b0, b1, b2, b3, k = (int(v) for v in args.batch_shape.split(","))
         cfg = L.lbm_batch_config_default(threads=th, stages=stg, band_rows=[b0, b1, b2, b3], steps_per_launch=k)
     else:
-        cfg = b.autotune(trial_steps=64)
+        cfg = b.autotune(trial_steps=128)  # long enough that trial noise does not flip the pick
     cfg.graph_launches = max(2, 2 * (64 // (2 * cfg.steps_per_launch)))
     b.set_config(cfg)
     warm = cfg.graph_launches * cfg.steps_per_launch
