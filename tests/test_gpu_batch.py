@@ -114,6 +114,39 @@ def test_results_do_not_depend_on_the_launch_shape():
     _close(cases)
 
 
+SPECS_CS = [
+    (512, 20, dict(theta="random", rates=dict(s_e=0.8, s_eps=0.8, s_j=1.0, s_q=1.1), t_over_tc=0.6)),
+    (512, 12, dict(theta="random", tau=0.8)),
+    (384, 16, dict(theta="random", t_over_tc=0.7, tau=0.9)),
+    (128, 24, dict(theta="random")),
+    (256, 10, dict(theta="random", tau=0.7)),
+]
+
+
+@pytest.mark.parametrize("threads", [256, 128])
+def test_specialised_kernels_match_the_generic_one(threads):
+    """A launch whose instances all share the Carnahan-Starling EOS and
+    geometric wetting runs the kernel with both fixed at compile time (and its
+    512-wide instances a sweep with the width fixed too).  The same instances
+    next to one Martys-Chen instance run the generic kernel; instances do not
+    interact, so every shared instance must come out with the same bits."""
+    cases = _cases(SPECS_CS, seed=11)
+    extra = _cases([(36, 12, dict(wetting=1, G_w=-0.1))], seed=12)
+    with _batch(cases, band_rows=[4, 8, 8, 8], steps_per_launch=4, threads=threads) as a, \
+            _batch(cases + extra, band_rows=[4, 8, 8, 8], steps_per_launch=4, threads=threads) as b:
+        a.step(9)
+        b.step(9)
+        assert a.status()[0] == 0 and b.status()[0] == 0
+        for ga, gb in zip(a.instances, b.instances):
+            assert np.array_equal(ga.f(), gb.f())
+        # and the specialised run against the oracle
+        for c, g in zip(cases, a.instances):
+            assert c.orc.step(9) == 0
+            fo, fg = c.orc.get_f(), g.f()
+            assert np.abs(fg - fo).max() < 2e-5 * np.abs(fo).max(), (c.nx, c.ny)
+    _close(cases + extra)
+
+
 def test_graph_replays_are_counted_and_match_direct_launches():
     import torch
 
