@@ -65,6 +65,16 @@ VARIANTS = {
     "piecewise_eos_ratio10": dict(eos="pw", pw=(0.25, -0.02, 0.3, 1.1216073327407194, 9.540106186999981)),
     "mrt_rates_kappa": dict(rates=dict(s_e=0.8, s_eps=0.9, s_j=1.0, s_q=1.1), kappa=0.9, A=-0.3),
     "low_T": dict(t_over_tc=0.5, tau=0.6, rates=dict(s_e=0.8, s_eps=0.8, s_j=1.0, s_q=1.1)),
+    # the remaining (collision, wetting, EOS) combinations the fused kernel is
+    # specialised on: general rates with Martys-Chen, and the piecewise EOS with
+    # general rates and with Martys-Chen (unit and general rates)
+    "martys_chen_mrt_rates": dict(wetting=1, G_w=-0.2, rates=dict(s_e=0.8, s_eps=0.9, s_j=1.0, s_q=1.1)),
+    "piecewise_mrt_rates": dict(eos="pw", pw=(0.25, -0.02, 0.3, 1.1216073327407194, 9.540106186999981),
+                                rates=dict(s_e=0.8, s_eps=0.9, s_j=1.0, s_q=1.1)),
+    "piecewise_martys_chen": dict(eos="pw", pw=(0.25, -0.02, 0.3, 1.1216073327407194, 9.540106186999981),
+                                  wetting=1, G_w=-0.1),
+    "piecewise_martys_chen_tau08": dict(eos="pw", pw=(0.25, -0.02, 0.3, 1.1216073327407194, 9.540106186999981),
+                                        wetting=1, G_w=-0.1, tau=0.8),
 }
 
 
